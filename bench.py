@@ -1,0 +1,306 @@
+"""Benchmark: Tabu moves evaluated per second on the paper-shaped instance.
+
+Workload (one "step"): one complete Tabu search of 5,000 iterations on the
+paper-shaped instance (12 bases, 20 vehicles, 60 clustered facilities in a
+1500 km box, 100 missions, tenure 10, duty cap 720 min as a penalty with lambda
+1000), greedy start included, through asched_solve. Every iteration evaluates all
+M(M+V-2) + M(M-1)/2 = 16,750 moves, so a step is 83.75 M moves.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank solves its own copy of the instance (the single-instance
+search does not shard); the line reports the sum of all ranks' moves over the
+slowest rank's time. `--impl reference` times the plain CPU oracle on this host's
+cores instead (bounded iteration samples of the same instance).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Tabu moves evaluated/sec (bit-exact); batched solves/sec and p50/p99 latency"
+UNIT = "moves/s"
+WORKLOAD = ("paper-shaped single instance: 12 bases, 20 vehicles, 60 facilities in 4 Gaussian "
+            "clusters (sigma 80 km) + 20% uniform outliers in a 1500 km box, 100 uniform missions, "
+            "int32 minutes at 250 km/h, duty cap 720 min (penalty, lambda 1000), tenure 10, "
+            "5,000 iterations, greedy start")
+# Algorithmic int32 operations per evaluated move (see the roofline section of the
+# design notes): a relocation is 23 ops, a swap 34, mixed in proportion.
+OPS_RELOCATE = 23
+OPS_SWAP = 34
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def moves_split(M, V):
+    return M * (M + V - 2), M * (M - 1) // 2
+
+
+class Clocks:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.index)], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.strip().split(", ") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_sample(inst, p, iterations):
+    """The oracle as it stands, one core, on the first `iterations` iterations."""
+    import oracle
+
+    pb = oracle.Problem(inst, p.cap_mode, p.lam)
+    t0 = time.perf_counter()
+    r = oracle.tabu_search(pb, p.tenure, iterations)
+    dt = time.perf_counter() - t0
+    assert r["status"] == 0
+    M, V = inst.n_missions, inst.n_vehicles
+    n = (M * (M + V - 2) + M * (M - 1) // 2) * iterations
+    return n / dt, dt
+
+
+def run_reference(args, rank, world):
+    from paper_2002_11710_gb300 import gen
+
+    if rank != 0:
+        return
+    inst, p = gen.paper_shaped(0), gen.PAPER_SHAPED_PARAMS
+    it_sample = args.ref_iterations
+    for _ in range(args.warmup):
+        cpu_oracle_sample(inst, p, it_sample)
+    rates, times = [], []
+    for _ in range(args.steps):
+        r, dt = cpu_oracle_sample(inst, p, it_sample)
+        rates.append(r)
+        times.append(dt)
+    M, V = inst.n_missions, inst.n_vehicles
+    n = (M * (M + V - 2) + M * (M - 1) // 2) * it_sample
+    value = n * len(times) / sum(times)
+    sample = f"first {it_sample} of 5,000 iterations of the paper-shaped instance per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample, "n_missions": M, "n_vehicles": V},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2002_11710_gb300 import api, gen
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    inst, p = gen.paper_shaped(0), gen.PAPER_SHAPED_PARAMS
+    M, V = inst.n_missions, inst.n_vehicles
+    R, S = moves_split(M, V)
+    moves_step = (R + S) * p.iterations
+    params = api.params_from(p, cluster_size=args.cluster, block_threads=args.threads)
+    dp = api.DeviceProblem(inst, dev)
+    plan = api.plan(dp, params)
+    out = api.alloc_output(dp, p.iterations)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)  # > 129 MB L2
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # warm-up (also checks the device status)
+    for _ in range(args.warmup):
+        api.solve(dp, params, out=out)
+    torch.cuda.synchronize()
+    info = out.info.cpu().numpy()
+    if info[api.INFO_STATUS] != 0:
+        raise RuntimeError(f"device status {info[api.INFO_STATUS]}")
+    z_best = int(info[api.INFO_Z_BEST])
+
+    clocks = Clocks(local_rank) if rank == 0 else None
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k)  # evict the previous step's data from L2 (not timed)
+        starts[k].record(stream)
+        api.solve(dp, params, out=out)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    dev_s = sum(step_ms) / 1000.0
+    clk = clocks.stop() if clocks else None
+    if world > 1:
+        t = torch.tensor([dev_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_s = float(t.item())
+    # end to end through the public API from host data
+    pinned = api.pin_instance(inst)
+    e2e_times = []
+    h2d = pinned.nbytes()
+    d2h = 0
+    for k in range(args.warmup + args.steps):
+        barrier()
+        flush.fill_(k)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        res = api.solve_host(pinned, params, device=dev)
+        t2 = time.perf_counter()
+        if k >= args.warmup:
+            e2e_times.append(t2 - t1)
+        d2h = sum(int(v.nbytes) for v in res.values())
+        assert int(res["info"][api.INFO_Z_BEST]) == z_best
+    e2e_s = sum(e2e_times)
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    if rank != 0:
+        return
+    value = moves_step * args.steps * world / dev_s
+    e2e_value = moves_step * args.steps * world / e2e_s
+    launch_s = statistics.mean(step_ms) / 1000.0
+    ops = (R * OPS_RELOCATE + S * OPS_SWAP) * p.iterations
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    int_lanes = args.int32_lanes_per_sm
+    peak_tops = sm_count * int_lanes * sm_max_mhz * 1e6 / 1e12
+    achieved = ops / launch_s / 1e12
+    cpu_rate, cpu_dt = cpu_oracle_sample(inst, p, args.cpu_iterations) if args.cpu_iterations > 0 else (None, 0)
+    lat = sorted(step_ms)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_missions": M, "n_vehicles": V,
+                   "iterations": p.iterations, "moves_per_iteration": R + S,
+                   "moves_per_step": moves_step, "cluster_size": plan.cluster_size,
+                   "block_threads": plan.block_threads, "smem_bytes": plan.smem_bytes,
+                   "l2": "flushed between steps (256 MB write, untimed)",
+                   "parallelism": "one instance per GPU (replicas)"},
+        "solves_per_s": world * args.steps / dev_s,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "wall_s": wall,
+        "z_best": z_best,
+        "gpu_launches": args.steps,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
+                     "frac": achieved / peak_tops, "traffic": None,
+                     "peak_basis": f"{sm_count} SMs x {int_lanes} int32 lanes/clk x {sm_max_mhz:.0f} MHz",
+                     "frac_of_sms_used": achieved / (peak_tops * plan.cluster_size / sm_count)},
+        "cpu_baseline": None if cpu_rate is None else {
+            "value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {args.cpu_iterations} of 5,000 iterations, same instance, {cpu_dt:.1f} s"},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--cluster", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--cpu-iterations", type=int, default=600)
+    ap.add_argument("--ref-iterations", type=int, default=100)
+    ap.add_argument("--int32-lanes-per-sm", type=int, default=128)
+    args = ap.parse_args()
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local_rank = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/*
+ * asched.h - C ABI of the GB300 (sm_103a) Tabu search for air-ambulance fleet
+ * scheduling (Tassone & Choudhury, "Algorithms for Optimizing Fleet Scheduling of
+ * Air Ambulances", arXiv 2002.11710).
+ *
+ * The problem (Section 3): vehicles sit on bases; a mission is a pickup -> delivery
+ * pair; each vehicle flies a closed route base -> p1 -> d1 -> ... -> pn -> dn -> base;
+ * every mission is flown exactly once; the objective is the total flight time (obj_s)
+ * under a per-vehicle duty cap (con6), optional arrive-by times (con7/con8) and
+ * helicopter-only missions (con9). The method improved here is the Tabu search of
+ * Algorithm 3 (Section 4.3), started from the greedy schedule of Algorithm 1
+ * (Section 4.1), widened to the whole neighbourhood each iteration:
+ *   R(m, y)   take mission m out of its route and put it immediately before node y;
+ *             a node is a mission (id 0..M-1) or the end of vehicle v's route (M+v);
+ *             y != m and y != the node after m.  Move id (m << 13) | y.
+ *   S(m1,m2)  m1 < m2 exchange places (also within one route).
+ *             Move id 0x80000000 | (m1 << 13) | m2.
+ * There are M(M+V-2) + M(M-1)/2 moves. Each iteration applies the admissible move
+ * with the least (delta, move id); admissible = feasible and (not tabu, or its
+ * objective is strictly below the best so far). Applying a move at iteration it
+ * makes (x, vehicle x left) tabu up to iteration it + tenure for every moved
+ * mission x; a move is tabu when it puts a mission x on a vehicle v with
+ * tabu_until[x][v] >= it. No admissible move: the iteration applies nothing.
+ *
+ * Conventions for every call below:
+ *   - "device" pointers are CUDA device memory owned by the caller (for example
+ *     PyTorch tensors); the library never allocates or frees memory and never
+ *     creates a stream or an event. Device buffers must stay valid until the work
+ *     queued on `stream` has finished.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Calls that launch work return as soon as it is queued.
+ *   - Every int32 array is dense and C-ordered. Travel times are integer minutes.
+ *   - Return value: ASCHED_OK, or a negative ASCHED_E_* for errors found on the host
+ *     before anything is queued (nothing is then written). Errors found on the
+ *     device are written to info[ASCHED_INFO_STATUS], readable once the stream has
+ *     been synchronised; the other outputs are then unspecified.
+ *   - The calls are thread-compatible: no global mutable state besides the per-kernel
+ *     attribute setup, which is idempotent.
+ */
+#ifndef ASCHED_H
+#define ASCHED_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ASCHED_ABI_VERSION 1
+
+/* Status codes. */
+#define ASCHED_OK 0
+#define ASCHED_E_INVALID (-1)          /* argument or instance data out of range */
+#define ASCHED_E_TOO_LARGE (-2)        /* instance does not fit the on-chip layout */
+#define ASCHED_E_OVERFLOW_GUARD (-3)   /* int32 objective could overflow (see below) */
+#define ASCHED_E_INFEASIBLE_INIT (-4)  /* no feasible initial schedule */
+#define ASCHED_E_TIMEOUT (-5)          /* a bounded device wait gave up */
+#define ASCHED_E_CUDA (-6)             /* a CUDA runtime call failed */
+
+/* Cap modes (the duty cap p of con6). */
+#define ASCHED_HARD 0     /* flight(v) <= duty_cap is a constraint */
+#define ASCHED_PENALTY 1  /* Z = sum flight + lambda * sum max(0, flight - duty_cap) */
+
+/* Per-move flags written by asched_eval_neighbourhood. */
+#define ASCHED_FLAG_FEASIBLE 1u
+#define ASCHED_FLAG_TABU 2u
+#define ASCHED_FLAG_ASPIRATION 4u  /* Z + delta < z_best */
+#define ASCHED_FLAG_ADMISSIBLE 8u
+
+#define ASCHED_SWAP_BIT 0x80000000u
+#define ASCHED_NULL_MOVE 0xFFFFFFFFu
+
+/* Layout of the int32 info[ASCHED_INFO_LEN] output. */
+#define ASCHED_INFO_STATUS 0   /* ASCHED_OK or a negative device-side status */
+#define ASCHED_INFO_Z_BEST 1   /* objective of the best schedule */
+#define ASCHED_INFO_BEST_IT 2  /* iteration that reached it (-1 = initial schedule) */
+#define ASCHED_INFO_Z_INIT 3   /* objective of the initial schedule */
+#define ASCHED_INFO_Z_FINAL 4  /* objective after the last iteration */
+#define ASCHED_INFO_ITERS 5    /* iterations completed */
+#define ASCHED_INFO_LEN 8
+
+/* One problem instance (Section 3). Sizes are host values; arrays are device memory.
+ *   travel    [n_types][n_loc][n_loc] minutes, every entry >= 0; type 0 = helicopter,
+ *             type 1 = plane (the l index of d_ijl in Eq. e1); n_types is 1 or 2.
+ *   veh_base  [n_vehicles] base location of each vehicle.
+ *   veh_type  [n_vehicles] 0 or 1 (b_k), or NULL for all helicopters.
+ *   pickup, delivery [n_missions] locations, pickup != delivery.
+ *   heli_only [n_missions] 1 = only a type-0 vehicle may fly it (rho), or NULL.
+ *   deadline  [n_missions] arrive-by minute at the delivery (w_n), or NULL for none.
+ *             With deadlines a vehicle leaves a delivery exactly at its w_n; a link
+ *             u -> m needs dep(u) + T[end u][p_m] + T[p_m][d_m] <= w_m (dep(base) = 0)
+ *             and the return needs dep(u) + T[end u][base] <= horizon.
+ *   duty_cap  p, flight minutes per vehicle; horizon: 1440 for a 24 h day. */
+typedef struct {
+  int32_t n_loc;
+  int32_t n_types;
+  int32_t n_vehicles;
+  int32_t n_missions;
+  const int32_t* travel;
+  const int32_t* veh_base;
+  const int32_t* veh_type;
+  const int32_t* pickup;
+  const int32_t* delivery;
+  const int32_t* heli_only;
+  const int32_t* deadline;
+  int32_t duty_cap;
+  int32_t horizon;
+} asched_instance;
+
+/* Search parameters.
+ *   tenure, iterations  >= 0.
+ *   cap_mode            ASCHED_HARD or ASCHED_PENALTY; lambda >= 0 (PENALTY weight).
+ *   cluster_size        CTAs cooperating on one instance (a thread-block cluster):
+ *                       0 = automatic, else 1, 2, 4, 8 or 16. Results do not depend
+ *                       on it.
+ *   block_threads       0 = automatic, else a multiple of 32 in [64, 1024].
+ *   timeout_ns          bound on every wait between CTAs; 0 = 1 s.
+ *   flags               must be 0. */
+typedef struct {
+  int32_t tenure;
+  int32_t iterations;
+  int32_t cap_mode;
+  int32_t lambda;
+  int32_t cluster_size;
+  int32_t block_threads;
+  int64_t timeout_ns;
+  uint32_t flags;
+} asched_params;
+
+/* Launch shape the library would use for an instance (see asched_plan). */
+typedef struct {
+  int32_t cluster_size;
+  int32_t block_threads;
+  int32_t smem_bytes;  /* dynamic shared memory per CTA */
+  int64_t moves_per_iteration;
+} asched_plan_t;
+
+/* Outputs of asched_solve; all device memory.
+ *   route_off [n_vehicles + 1], route [n_missions]: best schedule in CSR form; the
+ *             missions of vehicle v in flying order are route[route_off[v] ..
+ *             route_off[v+1]).
+ *   flight, overflow [n_vehicles]: minutes flown and minutes over duty_cap, best
+ *             schedule.
+ *   info      [ASCHED_INFO_LEN] (layout above).
+ *   traj_move [iterations] applied move id per iteration (ASCHED_NULL_MOVE when
+ *             none), or NULL; traj_z [iterations] objective after it, or NULL. */
+typedef struct {
+  int32_t* route_off;
+  int32_t* route;
+  int32_t* flight;
+  int32_t* overflow;
+  int32_t* info;
+  uint32_t* traj_move;
+  int32_t* traj_z;
+} asched_result;
+
+/* ABI version of the loaded library (ASCHED_ABI_VERSION). Never fails. */
+int asched_abi_version(void);
+
+/* Static text for a status code (never NULL). */
+const char* asched_status_string(int status);
+
+/* Number of canonical moves M(M+V-2) + M(M-1)/2 (Section 4.3 widened as above).
+ * Returns ASCHED_E_INVALID for negative sizes or NULL out. Host only. */
+int asched_num_moves(int32_t n_missions, int32_t n_vehicles, int64_t* out);
+
+/* Validate an instance whose arrays are HOST memory, with the checks the device
+ * prologue makes: index ranges, pickup != delivery, travel >= 0, n_types in {1,2},
+ * flags in {0,1}, and the int32 overflow guard
+ *   2 (2M + V + 2) max(travel) (1 + lambda) < 2^31.
+ * Returns ASCHED_OK or the status the device would report. Host only, no CUDA call. */
+int asched_check_instance_host(const asched_instance* inst, const asched_params* params);
+
+/* Launch shape and shared-memory footprint for the given sizes (array pointers are
+ * not read). Returns ASCHED_E_TOO_LARGE when the instance does not fit on chip,
+ * ASCHED_E_CUDA if the device cannot be queried. */
+int asched_plan(const asched_instance* inst, const asched_params* params, asched_plan_t* out);
+
+/* Tabu search (Algorithm 3) on one instance, all iterations in one persistent
+ * launch of `cluster_size` CTAs on `stream`.
+ *   init_route_off/init_route: device CSR initial schedule (must be feasible), or
+ *             both NULL to start from the greedy schedule of Algorithm 1 (heli-only
+ *             missions first, then by (deadline, id); each appended to the vehicle
+ *             with the least objective increase that stays feasible, lowest index on
+ *             ties).
+ * Device-side status: ASCHED_E_INVALID (bad data), ASCHED_E_OVERFLOW_GUARD,
+ * ASCHED_E_INFEASIBLE_INIT, ASCHED_E_TIMEOUT. */
+int asched_solve(const asched_instance* inst, const asched_params* params,
+                 const int32_t* init_route_off, const int32_t* init_route,
+                 const asched_result* out, void* stream);
+
+/* Every canonical move of one schedule, for checking (one launch, no move applied).
+ *   route_off/route  device CSR schedule (must be feasible).
+ *   tabu_until       device [n_missions][n_vehicles] int32, or NULL for none tabu.
+ *   it, z_best       iteration number and best objective for the tabu / aspiration
+ *                    tests.
+ *   delta_out        device [moves] int32: objective change of each move.
+ *   flags_out        device [moves] uint8: ASCHED_FLAG_* bits.
+ *   id_out           device [moves] uint32 move ids, or NULL.
+ *   best_key_out     device [1] uint64: ((delta ^ 0x80000000) << 32) | id of the
+ *                    move the search would apply, or all ones when none.
+ *   info             device [ASCHED_INFO_LEN].
+ * Moves are written in canonical order: R(m, y) by (m, y), then S(m1, m2) by
+ * (m1, m2), which is increasing move id. */
+int asched_eval_neighbourhood(const asched_instance* inst, const asched_params* params,
+                              const int32_t* route_off, const int32_t* route,
+                              const int32_t* tabu_until, int32_t it, int32_t z_best,
+                              int32_t* delta_out, uint8_t* flags_out, uint32_t* id_out,
+                              unsigned long long* best_key_out, int32_t* info, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ASCHED_H */

@@ -1,0 +1,1216 @@
+// asched.cu - GB300 (sm_103a) Tabu search for air-ambulance fleet scheduling.
+//
+// Method: Tassone & Choudhury, "Algorithms for Optimizing Fleet Scheduling of Air
+// Ambulances" (arXiv 2002.11710): model of Section 3 (obj_s, con1-con13), greedy
+// start of Algorithm 1 (Section 4.1), Tabu search of Algorithm 3 (Section 4.3)
+// widened to the whole relocate + swap neighbourhood every iteration. The readings
+// of the paper that fix the move set, move ids, tabu attribute, aspiration and
+// tie-break are stated in include/asched.h.
+//
+// Design (one instance per launch):
+//   * One persistent launch runs every iteration. The grid is one thread-block
+//     cluster of C CTAs (C = 1..16), one CTA per SM. Each CTA holds a complete copy
+//     of the instance and of the search state in shared memory and applies every
+//     move itself, so the only traffic between CTAs per iteration is one 64-bit key
+//     per CTA (DSMEM store + remote mbarrier arrive, bounded wait).
+//   * Shared memory holds two node-by-mission gather tables built once per launch:
+//       A[t][l][m] = T_t[l][p_m] + T_t[p_m][d_m]   (fly from location l to m's pickup, then m)
+//       B[t][l][m] = T_t[d_m][l]                   (from m's delivery to location l)
+//     with the mission index innermost and rows padded to a multiple of 32 words,
+//     so that 32 lanes reading 32 consecutive missions of any row hit 32 banks.
+//   * The schedule is a doubly linked list over nodes (missions 0..M-1 and route
+//     ends M..M+V-1), with per-node records (removal delta, gap leg, slot cost,
+//     table row offsets, cap slack, deadline slacks) in a double-buffered SoA.
+//     Applying a move rewrites every node's record from the previous buffer in one
+//     pass (one thread per node), so apply and preparation need no barrier between.
+//   * Every move (relocate (m, y) and swap (a, b)) is evaluated in O(1) from the
+//     records and the tables; the per-thread, warp (redux.sync), CTA (shared
+//     memory) and cluster (DSMEM) minimum of the key ((delta ^ 2^31) << 32) | id
+//     is independent of how moves are split over threads, so any launch shape
+//     gives the same trajectory.
+//   * The tabu list is a V x M table of iteration stamps in shared memory.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "asched.h"
+
+namespace {
+
+constexpr uint32_t kSwapBit = 0x80000000u;
+constexpr uint32_t kNullMove = 0xFFFFFFFFu;
+constexpr uint64_t kNoKey = ~0ull;
+constexpr int kMaxCluster = 16;
+constexpr int kIdShift = 13;
+constexpr uint32_t kIdMask = (1u << kIdShift) - 1u;
+constexpr int kMaxMissions = 4095;
+constexpr int kMaxNodes = 8192;
+constexpr int kMaxVehicles = 1024;
+constexpr int64_t kDefaultTimeoutNs = 1000000000ll;
+
+// ------------------------------------------------------------------ layout ---------
+
+constexpr int kStateArrays = 17;
+enum {
+  ST_NXT = 0, ST_PRV, ST_VEHP, ST_ROWA, ST_ROWB, ST_ROWBN, ST_ROWE, ST_INLEG, ST_REM,
+  ST_SLOT, ST_FBP, ST_SRCP, ST_DEPX, ST_YLIM, ST_YLIMN, ST_REMOK, ST_FL
+};
+
+struct Layout {  // offsets in int32 words from the start of dynamic shared memory
+  int A, B, tabu, cmat, wm, heli, eloc, sloc, vtype, st0, st1, best, order, cnt, gend,
+      gdep, gfl, glast, misc, warpkey, slots, mbar, total;
+  int Mp, Np, Vp;
+};
+
+__host__ __device__ inline int round_up(int x, int k) { return (x + k - 1) / k * k; }
+
+__host__ __device__ inline Layout make_layout(int M, int V, int L, int nt) {
+  Layout y;
+  y.Mp = round_up(M > 0 ? M : 1, 32);
+  y.Np = round_up(M + V, 4);
+  y.Vp = round_up(V, 4);
+  int o = 0;
+  y.A = o;       o += nt * L * y.Mp;
+  y.B = o;       o += nt * L * y.Mp;
+  y.tabu = o;    o += V * y.Mp;
+  y.cmat = o;    o += nt * y.Mp;
+  y.wm = o;      o += y.Mp;
+  y.heli = o;    o += y.Mp;
+  y.eloc = o;    o += y.Np;
+  y.sloc = o;    o += y.Np;
+  y.vtype = o;   o += y.Vp;
+  y.st0 = o;     o += kStateArrays * y.Np;
+  y.st1 = o;     o += kStateArrays * y.Np;
+  y.best = o;    o += y.Np;
+  y.order = o;   o += y.Mp;
+  y.cnt = o;     o += y.Mp;
+  y.gend = o;    o += y.Vp;
+  y.gdep = o;    o += y.Vp;
+  y.gfl = o;     o += y.Vp;
+  y.glast = o;   o += y.Vp;
+  y.misc = o;    o += 16;
+  o = round_up(o, 4);
+  y.warpkey = o; o += 2 * 32;
+  y.slots = o;   o += 2 * 2 * kMaxCluster;
+  y.mbar = o;    o += 4;
+  y.total = o;
+  return y;
+}
+
+// ------------------------------------------------------------------ parameters -----
+
+struct KParams {
+  const int32_t* travel;
+  const int32_t* veh_base;
+  const int32_t* veh_type;
+  const int32_t* pickup;
+  const int32_t* delivery;
+  const int32_t* heli_only;
+  const int32_t* deadline;
+  int32_t L, nt, V, M, cap, horizon;
+  int32_t tenure, iterations, lambda, cluster;
+  int64_t timeout_ns;
+  Layout lay;
+  const int32_t* init_off;
+  const int32_t* init_route;
+  const int32_t* tabu_in;
+  int32_t dbg_it, dbg_zbest;
+  int32_t* out_off;
+  int32_t* out_route;
+  int32_t* out_flight;
+  int32_t* out_over;
+  int32_t* info;
+  uint32_t* traj_move;
+  int32_t* traj_z;
+  int32_t* dbg_delta;
+  uint8_t* dbg_flags;
+  uint32_t* dbg_id;
+  unsigned long long* dbg_key;
+};
+
+// ------------------------------------------------------------------ PTX helpers ----
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t local_addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_addr), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void st_cluster_u64(uint32_t addr, uint64_t v) {
+  asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(addr), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the phase of `bar` with the given parity; false after timeout_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int64_t timeout_ns) {
+  const uint32_t addr = smem_u32(bar);
+  if (mbar_try_wait(addr, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (true) {
+    if (mbar_try_wait(addr, parity)) return true;
+    if ((int64_t)(global_ns() - t0) > timeout_ns) return false;
+  }
+}
+
+// ------------------------------------------------------------------ keys -----------
+
+__device__ __forceinline__ uint64_t pack_key(int32_t d, uint32_t id) {
+  return (static_cast<uint64_t>(static_cast<uint32_t>(d) ^ 0x80000000u) << 32) | id;
+}
+__device__ __forceinline__ int32_t key_delta(uint64_t k) {
+  return static_cast<int32_t>(static_cast<uint32_t>(k >> 32) ^ 0x80000000u);
+}
+
+__device__ __forceinline__ uint64_t warp_min_key(uint64_t k) {
+  const uint32_t hi = static_cast<uint32_t>(k >> 32), lo = static_cast<uint32_t>(k);
+  const uint32_t mhi = __reduce_min_sync(0xffffffffu, hi);
+  const uint32_t mlo = __reduce_min_sync(0xffffffffu, hi == mhi ? lo : 0xffffffffu);
+  return (static_cast<uint64_t>(mhi) << 32) | mlo;
+}
+
+__device__ __forceinline__ uint64_t min_u64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+__device__ __forceinline__ int32_t pos0(int32_t x) { return x > 0 ? x : 0; }
+
+// ------------------------------------------------------------------ shared state ---
+
+// One buffer of per-node records: array i of node t is base[i * np + t].
+struct State {
+  int32_t* base;
+  int np;
+  __device__ __forceinline__ int32_t* operator[](int i) const { return base + i * np; }
+};
+
+struct Smem {
+  int32_t* A;
+  int32_t* B;
+  int32_t* tabu;
+  int32_t* cmat;
+  int32_t* wm;
+  int32_t* heli;
+  int32_t* eloc;
+  int32_t* sloc;
+  int32_t* vtype;
+  int32_t* st_base;  // buffer 0; buffer 1 follows at st_stride words
+  int st_stride;
+  int np;
+  __device__ __forceinline__ State st(int k) const {
+    State s;
+    s.base = st_base + k * st_stride;
+    s.np = np;
+    return s;
+  }
+  int32_t* best;
+  int32_t* order;
+  int32_t* cnt;
+  int32_t* gend;
+  int32_t* gdep;
+  int32_t* gfl;
+  int32_t* glast;
+  int32_t* misc;
+  uint64_t* warpkey;
+  uint64_t* slots;
+  uint64_t* mbar;
+};
+
+__device__ inline Smem carve(int32_t* base, const Layout& y) {
+  Smem s;
+  s.A = base + y.A;
+  s.B = base + y.B;
+  s.tabu = base + y.tabu;
+  s.cmat = base + y.cmat;
+  s.wm = base + y.wm;
+  s.heli = base + y.heli;
+  s.eloc = base + y.eloc;
+  s.sloc = base + y.sloc;
+  s.vtype = base + y.vtype;
+  s.st_base = base + y.st0;
+  s.st_stride = y.st1 - y.st0;
+  s.np = y.Np;
+  s.best = base + y.best;
+  s.order = base + y.order;
+  s.cnt = base + y.cnt;
+  s.gend = base + y.gend;
+  s.gdep = base + y.gdep;
+  s.gfl = base + y.gfl;
+  s.glast = base + y.glast;
+  s.misc = base + y.misc;
+  s.warpkey = reinterpret_cast<uint64_t*>(base + y.warpkey);
+  s.slots = reinterpret_cast<uint64_t*>(base + y.slots);
+  s.mbar = reinterpret_cast<uint64_t*>(base + y.mbar);
+  return s;
+}
+
+// misc slots
+enum { MISC_BAD = 0, MISC_MAXT, MISC_Z0, MISC_GREEDY_FAIL, MISC_CSR_BAD };
+
+struct Ctx {  // per-launch constants every thread keeps in registers
+  int M, V, N, L, Mp, cap, horizon, lam;
+};
+
+// Rewrite every record of node t in state S2 from its links (nx, pv), its vehicle
+// word vp (vehicle | plane << 16) and the flight f2 of that vehicle.
+template <bool PEN, bool DL>
+__device__ __forceinline__ void write_records(const Smem& sm, const State& S2, const Ctx& c, int t,
+                                              int nx, int pv, int vp, int f2) {
+  const int vv = vp & 0xFFFF;
+  const int ty = sm.vtype[vv];
+  const int lb = ty * c.L;
+  const int rowA = (lb + sm.eloc[pv]) * c.Mp;
+  const int rowB = (lb + sm.sloc[t]) * c.Mp;
+  S2[ST_NXT][t] = nx;
+  S2[ST_PRV][t] = pv;
+  S2[ST_VEHP][t] = vp;
+  S2[ST_ROWA][t] = rowA;
+  S2[ST_ROWB][t] = rowB;
+  S2[ST_FBP][t] = f2 - c.cap;
+  if (DL) S2[ST_DEPX][t] = pv < c.M ? sm.wm[pv] : 0;
+  if (t < c.M) {
+    const int rowBn = (lb + sm.sloc[nx]) * c.Mp;
+    const int rowE = (lb + sm.eloc[t]) * c.Mp;
+    const int aT = sm.A[rowA + t];
+    const int bT = sm.B[rowBn + t];
+    const int slot = aT + bT;
+    const int* cm = sm.cmat + ty * c.Mp;
+    const int ct = cm[t];
+    const int leg = nx < c.M ? sm.A[rowA + nx] - cm[nx] : (pv < c.M ? sm.B[rowBn + pv] : 0);
+    const int rem = leg - slot;
+    const int fb = f2 - c.cap;
+    S2[ST_ROWBN][t] = rowBn;
+    S2[ST_ROWE][t] = rowE;
+    S2[ST_SLOT][t] = slot;
+    S2[ST_REM][t] = rem;
+    S2[ST_INLEG][t] = aT - ct;
+    S2[ST_SRCP][t] = PEN ? pos0(fb + rem) - pos0(fb) : fb + rem;
+    if (DL) {
+      const int dep = pv < c.M ? sm.wm[pv] : 0;
+      S2[ST_YLIM][t] = sm.wm[t] - ct;
+      S2[ST_YLIMN][t] = nx < c.M ? sm.wm[nx] - cm[nx] : c.horizon;
+      const int lim = nx < c.M ? sm.wm[nx] : c.horizon;
+      const int add = nx < c.M ? cm[nx] : 0;
+      S2[ST_REMOK][t] = (dep + leg + add <= lim) ? 1 : 0;
+    }
+  } else {
+    S2[ST_INLEG][t] = (pv == t) ? 0 : sm.B[rowB + pv];
+    if (DL) S2[ST_YLIM][t] = c.horizon;
+  }
+}
+
+// Relocation R(m, y): take m out, put it immediately before node y.
+template <bool PEN, bool DL, bool DEBUG>
+__device__ __forceinline__ uint64_t eval_relocate(const Smem& sm, const State& S, const Ctx& c, int y,
+                                                  int m, int it, int Z, int zbest, const KParams& P) {
+  const int s_m = S[ST_NXT][m];
+  if (y == m || y == s_m) return kNoKey;
+  const int vpy = S[ST_VEHP][y], vpm = S[ST_VEHP][m];
+  const int vy = vpy & 0xFFFF, vm = vpm & 0xFFFF;
+  const int a = sm.A[S[ST_ROWA][y] + m];
+  const int b = sm.B[S[ST_ROWB][y] + m];
+  const int ins = a + b - S[ST_INLEG][y];
+  const int rem = S[ST_REM][m];
+  const int fy = S[ST_FBP][y];
+  int delta;
+  bool feas;
+  if (vm == vy) {
+    const int d = rem + ins;
+    if (PEN) {
+      delta = d + c.lam * (pos0(fy + d) - pos0(fy));
+      feas = true;
+    } else {
+      delta = d;
+      feas = fy + d <= 0;
+    }
+  } else {
+    const int sp = S[ST_SRCP][m];
+    if (PEN) {
+      delta = rem + ins + c.lam * (sp + pos0(fy + ins) - pos0(fy));
+      feas = true;
+    } else {
+      delta = rem + ins;
+      feas = (sp <= 0) && (fy + ins <= 0);
+    }
+  }
+  feas = feas && !(sm.heli[m] && (vpy >> 16));
+  if (DL) {
+    const int w = sm.wm[m];
+    feas = feas && (S[ST_DEPX][y] + a <= w) && (w + b <= S[ST_YLIM][y]) && S[ST_REMOK][m];
+  }
+  const bool tabu = sm.tabu[vy * c.Mp + m] >= it;
+  const bool asp = Z + delta < zbest;
+  const bool adm = feas && (!tabu || asp);
+  const uint32_t id = (static_cast<uint32_t>(m) << kIdShift) | static_cast<uint32_t>(y);
+  if (DEBUG) {
+    const int64_t idx = static_cast<int64_t>(m) * (c.N - 2) + y - (y > m) - (y > s_m);
+    P.dbg_delta[idx] = delta;
+    P.dbg_flags[idx] = static_cast<uint8_t>((feas ? 1 : 0) | (tabu ? 2 : 0) | (asp ? 4 : 0) | (adm ? 8 : 0));
+    if (P.dbg_id) P.dbg_id[idx] = id;
+  }
+  return adm ? pack_key(delta, id) : kNoKey;
+}
+
+// Swap S(a, b): the two missions exchange places.
+template <bool PEN, bool DL, bool DEBUG>
+__device__ __forceinline__ uint64_t eval_swap(const Smem& sm, const State& S, const Ctx& c, int a, int b,
+                                              int it, int Z, int zbest, const KParams& P) {
+  const int vpa = S[ST_VEHP][a], vpb = S[ST_VEHP][b];
+  const int va = vpa & 0xFFFF, vb = vpb & 0xFFFF;
+  const int na = S[ST_NXT][a], nb = S[ST_NXT][b];
+  const bool adjA = (na == b), adjB = (nb == a);
+  const int t1 = sm.A[(adjB ? S[ST_ROWE][a] : S[ST_ROWA][a]) + b];
+  const int t2 = sm.B[S[ST_ROWBN][a] + (adjA ? a : b)];
+  const int t3 = sm.A[(adjA ? S[ST_ROWE][b] : S[ST_ROWA][b]) + a];
+  const int t4 = sm.B[S[ST_ROWBN][b] + (adjB ? b : a)];
+  const int da = t1 + t2 - S[ST_SLOT][a];
+  const int db = t3 + t4 - S[ST_SLOT][b];
+  const int fa = S[ST_FBP][a], fb = S[ST_FBP][b];
+  int delta;
+  bool feas;
+  if (va == vb) {
+    const int d = da + db;
+    if (PEN) {
+      delta = d + c.lam * (pos0(fa + d) - pos0(fa));
+      feas = true;
+    } else {
+      delta = d;
+      feas = fa + d <= 0;
+    }
+  } else {
+    if (PEN) {
+      delta = da + db + c.lam * (pos0(fa + da) - pos0(fa) + pos0(fb + db) - pos0(fb));
+      feas = true;
+    } else {
+      delta = da + db;
+      feas = (fa + da <= 0) && (fb + db <= 0);
+    }
+  }
+  feas = feas && !((sm.heli[a] && (vpb >> 16)) || (sm.heli[b] && (vpa >> 16)));
+  if (DL) {
+    const int wa = sm.wm[a], wb = sm.wm[b];
+    const bool l1 = (adjB ? wa : S[ST_DEPX][a]) + t1 <= wb;
+    const bool l2 = adjA || (wb + t2 <= S[ST_YLIMN][a]);
+    const bool l3 = (adjA ? wb : S[ST_DEPX][b]) + t3 <= wa;
+    const bool l4 = adjB || (wa + t4 <= S[ST_YLIMN][b]);
+    feas = feas && l1 && l2 && l3 && l4;
+  }
+  const bool tabu = (sm.tabu[vb * c.Mp + a] >= it) || (sm.tabu[va * c.Mp + b] >= it);
+  const bool asp = Z + delta < zbest;
+  const bool adm = feas && (!tabu || asp);
+  const int m1 = a < b ? a : b, m2 = a < b ? b : a;
+  const uint32_t id = kSwapBit | (static_cast<uint32_t>(m1) << kIdShift) | static_cast<uint32_t>(m2);
+  if (DEBUG) {
+    const int64_t rtot = static_cast<int64_t>(c.M) * (c.N - 2);
+    const int64_t idx = rtot + static_cast<int64_t>(m1) * (2 * c.M - m1 - 1) / 2 + (m2 - m1 - 1);
+    P.dbg_delta[idx] = delta;
+    P.dbg_flags[idx] = static_cast<uint8_t>((feas ? 1 : 0) | (tabu ? 2 : 0) | (asp ? 4 : 0) | (adm ? 8 : 0));
+    if (P.dbg_id) P.dbg_id[idx] = id;
+  }
+  return adm ? pack_key(delta, id) : kNoKey;
+}
+
+// ------------------------------------------------------------------ the kernel -----
+
+template <bool PEN, bool DL, bool DEBUG>
+__global__ void __launch_bounds__(1024, 1) tabu_kernel(const __grid_constant__ KParams P) {
+  extern __shared__ __align__(16) int32_t smem_raw[];
+  const Smem sm = carve(smem_raw, P.lay);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
+  const int C = P.cluster;
+  const int rank = C > 1 ? static_cast<int>(cluster_rank()) : 0;
+  Ctx c;
+  c.M = P.M;
+  c.V = P.V;
+  c.N = P.M + P.V;
+  c.L = P.L;
+  c.Mp = P.lay.Mp;
+  c.cap = P.cap;
+  c.horizon = P.horizon;
+  c.lam = P.lambda;
+  const int M = c.M, V = c.V, N = c.N, L = c.L, Mp = c.Mp, nt = P.nt;
+  int status = ASCHED_OK;
+
+  // ---- prologue 1: static per-mission / per-node data and validation
+  if (tid < 16) sm.misc[tid] = 0;
+  __syncthreads();
+  int bad = 0;
+  for (int i = tid; i < Mp; i += nthr) {
+    if (i < M) {
+      const int p = P.pickup[i], d = P.delivery[i];
+      const int h = P.heli_only ? P.heli_only[i] : 0;
+      bad |= (p < 0) | (p >= L) | (d < 0) | (d >= L) | (p == d) | (h < 0) | (h > 1);
+      sm.wm[i] = P.deadline ? P.deadline[i] : 0;
+      sm.heli[i] = h;
+      sm.eloc[i] = d;
+      sm.sloc[i] = p;
+      sm.cnt[i] = 0;
+    } else {
+      sm.wm[i] = 0;
+      sm.heli[i] = 0;
+    }
+  }
+  for (int v = tid; v < V; v += nthr) {
+    const int b = P.veh_base[v];
+    const int ty = P.veh_type ? P.veh_type[v] : 0;
+    bad |= (b < 0) | (b >= L) | (ty < 0) | (ty >= nt);
+    sm.eloc[M + v] = b;
+    sm.sloc[M + v] = b;
+    sm.vtype[v] = ty;
+  }
+  int maxT = 0;
+  for (int i = tid; i < nt * L * L; i += nthr) {
+    const int x = P.travel[i];
+    bad |= x < 0;
+    maxT = x > maxT ? x : maxT;
+  }
+  maxT = __reduce_max_sync(0xffffffffu, maxT);
+  if (lane == 0) atomicMax(&sm.misc[MISC_MAXT], maxT);
+  if (__syncthreads_or(bad)) status = ASCHED_E_INVALID;
+  if (status == ASCHED_OK) {
+    // 2 (2M + V + 2) maxT (1 + lambda) < 2^31 keeps every int32 sum in range.
+    const double bound = 2.0 * (2.0 * M + V + 2.0) * static_cast<double>(sm.misc[MISC_MAXT]) *
+                         (1.0 + (PEN ? static_cast<double>(c.lam) : 0.0));
+    if (!(bound < 2147483648.0)) status = ASCHED_E_OVERFLOW_GUARD;
+  }
+
+  // ---- prologue 2: gather tables, in-mission legs, tabu stamps
+  if (status == ASCHED_OK) {
+    for (int i = tid; i < nt * L * Mp; i += nthr) {
+      const int r = i / Mp, m = i - r * Mp;
+      const int t = r / L, l = r - t * L;
+      int av = 0, bv = 0;
+      if (m < M) {
+        const int32_t* T = P.travel + static_cast<int64_t>(t) * L * L;
+        const int p = sm.sloc[m], d = sm.eloc[m];
+        av = T[l * L + p] + T[p * L + d];
+        bv = T[d * L + l];
+      }
+      sm.A[i] = av;
+      sm.B[i] = bv;
+    }
+    for (int i = tid; i < nt * Mp; i += nthr) {
+      const int t = i / Mp, m = i - t * Mp;
+      int cv = 0;
+      if (m < M) {
+        const int32_t* T = P.travel + static_cast<int64_t>(t) * L * L;
+        cv = T[sm.sloc[m] * L + sm.eloc[m]];
+      }
+      sm.cmat[i] = cv;
+    }
+    for (int i = tid; i < V * Mp; i += nthr) {
+      const int v = i / Mp, m = i - v * Mp;
+      sm.tabu[i] = (P.tabu_in && m < M) ? P.tabu_in[static_cast<int64_t>(m) * V + v] : -1;
+    }
+    // links of route ends; vehicle words
+    const State S0 = sm.st(0);
+    for (int v = tid; v < V; v += nthr) {
+      S0[ST_NXT][M + v] = M + v;
+      S0[ST_PRV][M + v] = M + v;
+      S0[ST_VEHP][M + v] = v | ((sm.vtype[v] != 0 ? 1 : 0) << 16);
+    }
+  }
+  __syncthreads();
+
+  // ---- prologue 3: initial schedule (caller's CSR, or Algorithm 1 on the device)
+  if (status == ASCHED_OK) {
+    const State S0 = sm.st(0);
+    if (P.init_off) {
+      int csr_bad = 0;
+      for (int v = tid; v < V; v += nthr) {
+        const int o0 = P.init_off[v], o1 = P.init_off[v + 1];
+        if (o0 < 0 || o1 < o0 || o1 > M || (v == 0 && o0 != 0) || (v == V - 1 && o1 != M)) {
+          csr_bad = 1;
+          continue;
+        }
+        int prev = M + v;
+        const int vp = v | ((sm.vtype[v] != 0 ? 1 : 0) << 16);
+        for (int k = o0; k < o1; ++k) {
+          const int m = P.init_route[k];
+          if (m < 0 || m >= M) {
+            csr_bad = 1;
+            break;
+          }
+          atomicAdd(&sm.cnt[m], 1);
+          S0[ST_NXT][prev] = m;
+          S0[ST_PRV][m] = prev;
+          S0[ST_VEHP][m] = vp;
+          prev = m;
+        }
+        S0[ST_NXT][prev] = M + v;
+        S0[ST_PRV][M + v] = prev;
+      }
+      csr_bad = __syncthreads_or(csr_bad);
+      if (!csr_bad) {
+        int dup = 0;
+        for (int m = tid; m < M; m += nthr) dup |= sm.cnt[m] != 1;
+        csr_bad = __syncthreads_or(dup);
+      }
+      if (csr_bad) status = ASCHED_E_INVALID;
+    } else {
+      // Mission order: heli-only first, then by deadline, then by id.
+      for (int m = tid; m < M; m += nthr) {
+        const int hm = sm.heli[m] ? 0 : 1, wmv = DL ? sm.wm[m] : 0;
+        int r = 0;
+        for (int k = 0; k < M; ++k) {
+          const int hk = sm.heli[k] ? 0 : 1, wk = DL ? sm.wm[k] : 0;
+          r += (hk < hm) || (hk == hm && (wk < wmv || (wk == wmv && k < m)));
+        }
+        sm.order[r] = m;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        for (int v = lane; v < V; v += 32) {
+          sm.glast[v] = M + v;
+          sm.gend[v] = sm.eloc[M + v];
+          sm.gdep[v] = 0;
+          sm.gfl[v] = 0;
+        }
+        __syncwarp();
+        int fail = 0;
+        for (int k = 0; k < M && !fail; ++k) {
+          const int m = sm.order[k];
+          const int w = sm.wm[m];
+          uint64_t best = kNoKey;
+          for (int v = lane; v < V; v += 32) {
+            const int ty = sm.vtype[v];
+            const int lb = ty * L;
+            const int bl = sm.eloc[M + v];
+            const int a = sm.A[(lb + sm.gend[v]) * Mp + m];
+            const int bret = sm.B[(lb + bl) * Mp + m];
+            const int last = sm.glast[v];
+            const int old = last == M + v ? 0 : sm.B[(lb + bl) * Mp + last];
+            const int app = a + bret - old;
+            const int f = sm.gfl[v];
+            bool ok = !(sm.heli[m] && ty != 0);
+            if (DL) ok = ok && (sm.gdep[v] + a <= w) && (w + bret <= c.horizon);
+            int score;
+            if (PEN) {
+              score = app + c.lam * (pos0(f + app - c.cap) - pos0(f - c.cap));
+            } else {
+              ok = ok && (f + app <= c.cap);
+              score = app;
+            }
+            if (ok) best = min_u64(best, pack_key(score, static_cast<uint32_t>(v)));
+          }
+          best = warp_min_key(best);
+          if (best == kNoKey) {
+            fail = 1;
+            break;
+          }
+          if (lane == 0) {
+            const int v = static_cast<int>(static_cast<uint32_t>(best));
+            const int ty = sm.vtype[v];
+            const int lb = ty * L;
+            const int bl = sm.eloc[M + v];
+            const int last = sm.glast[v];
+            const int a = sm.A[(lb + sm.gend[v]) * Mp + m];
+            const int bret = sm.B[(lb + bl) * Mp + m];
+            const int old = last == M + v ? 0 : sm.B[(lb + bl) * Mp + last];
+            S0[ST_NXT][last] = m;
+            S0[ST_PRV][m] = last;
+            S0[ST_NXT][m] = M + v;
+            S0[ST_PRV][M + v] = m;
+            S0[ST_VEHP][m] = S0[ST_VEHP][M + v];
+            sm.glast[v] = m;
+            sm.gend[v] = sm.eloc[m];
+            sm.gdep[v] = w;
+            sm.gfl[v] += a + bret - old;
+          }
+          __syncwarp();
+        }
+        if (lane == 0) sm.misc[MISC_GREEDY_FAIL] = fail;
+      }
+      __syncthreads();
+      if (sm.misc[MISC_GREEDY_FAIL]) status = ASCHED_E_INFEASIBLE_INIT;
+    }
+  }
+
+  // ---- prologue 4: flights, records, initial objective and feasibility
+  int Z = 0;
+  if (status == ASCHED_OK) {
+    const State S0 = sm.st(0);
+    for (int v = tid; v < V; v += nthr) S0[ST_FL][v] = 0;
+    __syncthreads();
+    for (int t = tid; t < N; t += nthr) {
+      const int pv = S0[ST_PRV][t];
+      const int vv = S0[ST_VEHP][t] & 0xFFFF;
+      const int lb = sm.vtype[vv] * L;
+      int contrib;
+      if (t < M) contrib = sm.A[(lb + sm.eloc[pv]) * Mp + t];
+      else contrib = pv == t ? 0 : sm.B[(lb + sm.sloc[t]) * Mp + pv];
+      atomicAdd(&S0[ST_FL][vv], contrib);
+    }
+    __syncthreads();
+    int infeasible = 0;
+    for (int t = tid; t < N; t += nthr) {
+      const int vp = S0[ST_VEHP][t];
+      const int vv = vp & 0xFFFF;
+      const int f = S0[ST_FL][vv];
+      write_records<PEN, DL>(sm, S0, c, t, S0[ST_NXT][t], S0[ST_PRV][t], vp, f);
+      const int pv = S0[ST_PRV][t];
+      if (t < M) {
+        infeasible |= sm.heli[t] && (vp >> 16);
+        if (DL) {
+          const int lb = sm.vtype[vv] * L;
+          const int dep = pv < M ? sm.wm[pv] : 0;
+          infeasible |= dep + sm.A[(lb + sm.eloc[pv]) * Mp + t] > sm.wm[t];
+        }
+      } else {
+        if (!PEN) infeasible |= f > c.cap;
+        if (DL && pv != t) {
+          const int lb = sm.vtype[vv] * L;
+          infeasible |= sm.wm[pv] + sm.B[(lb + sm.sloc[t]) * Mp + pv] > c.horizon;
+        }
+      }
+    }
+    if (__syncthreads_or(infeasible)) status = ASCHED_E_INFEASIBLE_INIT;
+    if (warp == 0) {
+      int z = 0;
+      for (int v = lane; v < V; v += 32) {
+        const int f = S0[ST_FL][v];
+        z += f + (PEN ? c.lam * pos0(f - c.cap) : 0);
+      }
+      z = __reduce_add_sync(0xffffffffu, z);
+      if (lane == 0) sm.misc[MISC_Z0] = z;
+    }
+    for (int t = tid; t < N; t += nthr) sm.best[t] = S0[ST_NXT][t];
+    if (tid == 0 && C > 1) {
+      mbar_init(&sm.mbar[0], static_cast<uint32_t>(C));
+      mbar_init(&sm.mbar[1], static_cast<uint32_t>(C));
+      fence_mbar_init();
+    }
+    __syncthreads();
+    Z = sm.misc[MISC_Z0];
+  }
+
+  // ---- main loop
+  int zbest = Z, best_it = -1, it = 0, cur = 0;
+  const bool looped = status == ASCHED_OK;  // uniform over the cluster
+  if (looped) {
+    if (C > 1) cluster_sync_all();
+    const int G = C * nthr;
+    const int g = rank * nthr + tid;
+    const int64_t Rn = static_cast<int64_t>(N) * M;
+    const int64_t Sn = static_cast<int64_t>(M) * (M - 1) / 2;
+    const int iters = DEBUG ? 1 : P.iterations;
+    for (it = 0; it < iters; ++it) {
+      const State S = sm.st(cur);
+      const int it_eval = DEBUG ? P.dbg_it : it;
+      const int zb_eval = DEBUG ? P.dbg_zbest : zbest;
+      uint64_t key = kNoKey;
+      for (int64_t i = g; i < Rn; i += G) {
+        const int y = static_cast<int>(i / M);
+        const int m = static_cast<int>(i - static_cast<int64_t>(y) * M);
+        key = min_u64(key, eval_relocate<PEN, DL, DEBUG>(sm, S, c, y, m, it_eval, Z, zb_eval, P));
+      }
+      for (int64_t j = g; j < Sn; j += G) {
+        const int row = static_cast<int>(j / M);
+        const int a = static_cast<int>(j - static_cast<int64_t>(row) * M);
+        int b = a + row + 1;
+        if (b >= M) b -= M;
+        key = min_u64(key, eval_swap<PEN, DL, DEBUG>(sm, S, c, a, b, it_eval, Z, zb_eval, P));
+      }
+      key = warp_min_key(key);
+      if (lane == 0) sm.warpkey[warp] = key;
+      __syncthreads();
+      uint64_t gk = warp_min_key(lane < nwarps ? sm.warpkey[lane] : kNoKey);
+      bool timed_out = false;
+      if (C > 1) {
+        const int sb = it & 1;
+        if (warp == 0 && lane < C) {
+          const uint32_t slot_addr = smem_u32(&sm.slots[sb * kMaxCluster + rank]);
+          const uint32_t bar_addr = smem_u32(&sm.mbar[sb]);
+          st_cluster_u64(mapa_rank(slot_addr, lane), gk);
+          mbar_arrive_cluster(mapa_rank(bar_addr, lane));
+        }
+        // The decision must be warp-uniform before the warp-wide reduction below.
+        const bool ok = __all_sync(0xffffffffu,
+                                   mbar_wait_bounded(&sm.mbar[sb], static_cast<uint32_t>((it >> 1) & 1),
+                                                     P.timeout_ns));
+        if (!ok) {
+          timed_out = true;
+        } else {
+          gk = warp_min_key(lane < C ? sm.slots[sb * kMaxCluster + lane] : kNoKey);
+        }
+      }
+      if (DEBUG) {
+        if (rank == 0 && tid == 0 && !timed_out) *P.dbg_key = gk;
+      } else if (!timed_out && gk != kNoKey) {
+        // ---- apply the chosen move: every thread decodes it, then rewrites its nodes
+        const State S2 = sm.st(cur ^ 1);
+        const uint32_t id = static_cast<uint32_t>(gk);
+        const bool is_swap = (id & kSwapBit) != 0;
+        int m = 0, y = 0, e = 0, s = 0, x = 0, a = 0, b = 0, pa = 0, na = 0, pb = 0, nb = 0;
+        bool adjA = false, adjB = false;
+        int va, vb, vpa, vpb, fa2, fb2 = 0;
+        if (!is_swap) {
+          m = static_cast<int>(id >> kIdShift);
+          y = static_cast<int>(id & kIdMask);
+          e = S[ST_PRV][m];
+          s = S[ST_NXT][m];
+          x = S[ST_PRV][y];
+          vpa = S[ST_VEHP][m];
+          vpb = S[ST_VEHP][y];
+          va = vpa & 0xFFFF;
+          vb = vpb & 0xFFFF;
+          const int ins = sm.A[S[ST_ROWA][y] + m] + sm.B[S[ST_ROWB][y] + m] - S[ST_INLEG][y];
+          const int rem = S[ST_REM][m];
+          const int fa = S[ST_FL][va];
+          if (va == vb) {
+            fa2 = fa + rem + ins;
+          } else {
+            fa2 = fa + rem;
+            fb2 = S[ST_FL][vb] + ins;
+          }
+        } else {
+          a = static_cast<int>((id >> kIdShift) & kIdMask);
+          b = static_cast<int>(id & kIdMask);
+          vpa = S[ST_VEHP][a];
+          vpb = S[ST_VEHP][b];
+          va = vpa & 0xFFFF;
+          vb = vpb & 0xFFFF;
+          pa = S[ST_PRV][a];
+          na = S[ST_NXT][a];
+          pb = S[ST_PRV][b];
+          nb = S[ST_NXT][b];
+          adjA = na == b;
+          adjB = nb == a;
+          const int t1 = sm.A[(adjB ? S[ST_ROWE][a] : S[ST_ROWA][a]) + b];
+          const int t2 = sm.B[S[ST_ROWBN][a] + (adjA ? a : b)];
+          const int t3 = sm.A[(adjA ? S[ST_ROWE][b] : S[ST_ROWA][b]) + a];
+          const int t4 = sm.B[S[ST_ROWBN][b] + (adjB ? b : a)];
+          const int da = t1 + t2 - S[ST_SLOT][a];
+          const int db = t3 + t4 - S[ST_SLOT][b];
+          const int fa = S[ST_FL][va];
+          if (va == vb) {
+            fa2 = fa + da + db;
+          } else {
+            fa2 = fa + da;
+            fb2 = S[ST_FL][vb] + db;
+          }
+        }
+        const int Znew = Z + key_delta(gk);
+        const bool improved = Znew < zbest;
+        for (int t = tid; t < N; t += nthr) {
+          int nx = S[ST_NXT][t], pv = S[ST_PRV][t], vp = S[ST_VEHP][t];
+          if (!is_swap) {
+            if (t == e) nx = s;
+            if (t == s) pv = e;
+            if (t == x) nx = m;
+            if (t == y) pv = m;
+            if (t == m) {
+              nx = y;
+              pv = x;
+              vp = vpb;
+            }
+          } else if (adjA) {  // pa -> a -> b -> nb  becomes  pa -> b -> a -> nb
+            if (t == pa) nx = b;
+            if (t == nb) pv = a;
+            if (t == b) {
+              pv = pa;
+              nx = a;
+            }
+            if (t == a) {
+              pv = b;
+              nx = nb;
+            }
+          } else if (adjB) {  // pb -> b -> a -> na  becomes  pb -> a -> b -> na
+            if (t == pb) nx = a;
+            if (t == na) pv = b;
+            if (t == a) {
+              pv = pb;
+              nx = b;
+            }
+            if (t == b) {
+              pv = a;
+              nx = na;
+            }
+          } else {
+            if (t == pa) nx = b;
+            if (t == na) pv = b;
+            if (t == pb) nx = a;
+            if (t == nb) pv = a;
+            if (t == a) {
+              pv = pb;
+              nx = nb;
+              vp = vpb;
+            }
+            if (t == b) {
+              pv = pa;
+              nx = na;
+              vp = vpa;
+            }
+          }
+          const int vv = vp & 0xFFFF;
+          const int f2 = vv == va ? fa2 : (vv == vb ? fb2 : S[ST_FL][vv]);
+          write_records<PEN, DL>(sm, S2, c, t, nx, pv, vp, f2);
+          if (t >= M) S2[ST_FL][t - M] = f2;
+          if (improved) sm.best[t] = nx;
+        }
+        if (tid == 0) {
+          if (!is_swap) {
+            sm.tabu[va * Mp + m] = it + P.tenure;
+          } else {
+            sm.tabu[va * Mp + a] = it + P.tenure;
+            sm.tabu[vb * Mp + b] = it + P.tenure;
+          }
+        }
+        Z = Znew;
+        if (improved) {
+          zbest = Znew;
+          best_it = it;
+        }
+      }
+      if (!DEBUG && rank == 0 && tid == 0 && !timed_out) {
+        if (P.traj_move) P.traj_move[it] = gk == kNoKey ? kNullMove : static_cast<uint32_t>(gk);
+        if (P.traj_z) P.traj_z[it] = Z;
+      }
+      if (__syncthreads_or(timed_out)) {
+        status = ASCHED_E_TIMEOUT;
+        break;
+      }
+      if (!DEBUG && gk != kNoKey) cur ^= 1;
+    }
+  }
+
+  // ---- epilogue: best schedule in CSR form (rank 0 writes every output)
+  if (rank == 0 && !DEBUG && status == ASCHED_OK && P.out_off) {
+    int* lens = sm.order;  // scratch reuse
+    int walk_bad = 0;
+    for (int v = tid; v < V; v += nthr) {
+      int n = 0, t = sm.best[M + v];
+      while (t != M + v && n <= M) {
+        if (t < 0 || t >= M) {
+          walk_bad = 1;
+          break;
+        }
+        ++n;
+        t = sm.best[t];
+      }
+      lens[v] = n;
+      walk_bad |= n > M;
+    }
+    walk_bad = __syncthreads_or(walk_bad);
+    if (tid == 0 && !walk_bad) {
+      int o = 0;
+      for (int v = 0; v < V; ++v) {
+        P.out_off[v] = o;
+        o += lens[v];
+      }
+      P.out_off[V] = o;
+      walk_bad = o != M;
+      sm.misc[MISC_CSR_BAD] = walk_bad;
+    }
+    __syncthreads();
+    if (sm.misc[MISC_CSR_BAD]) walk_bad = 1;
+    if (!walk_bad) {
+      for (int v = tid; v < V; v += nthr) {
+        const int ty = sm.vtype[v];
+        const int32_t* T = P.travel + static_cast<int64_t>(ty) * L * L;
+        const int bl = sm.eloc[M + v];
+        int o = 0;
+        for (int w = 0; w < v; ++w) o += lens[w];
+        int f = 0, prevloc = bl, t = sm.best[M + v];
+        while (t != M + v) {
+          P.out_route[o++] = t;
+          f += T[prevloc * L + sm.sloc[t]] + T[sm.sloc[t] * L + sm.eloc[t]];
+          prevloc = sm.eloc[t];
+          t = sm.best[t];
+        }
+        if (lens[v] > 0) f += T[prevloc * L + bl];
+        if (P.out_flight) P.out_flight[v] = f;
+        if (P.out_over) P.out_over[v] = pos0(f - c.cap);
+      }
+    } else {
+      status = ASCHED_E_INVALID;
+    }
+  }
+  if (rank == 0 && tid == 0 && P.info) {
+    P.info[ASCHED_INFO_STATUS] = status;
+    P.info[ASCHED_INFO_Z_BEST] = zbest;
+    P.info[ASCHED_INFO_BEST_IT] = best_it;
+    P.info[ASCHED_INFO_Z_INIT] = status == ASCHED_OK || status == ASCHED_E_TIMEOUT ? sm.misc[MISC_Z0] : 0;
+    P.info[ASCHED_INFO_Z_FINAL] = Z;
+    P.info[ASCHED_INFO_ITERS] = it;
+    P.info[6] = 0;
+    P.info[7] = 0;
+  }
+  // No CTA may leave while a peer can still write into its shared memory.
+  if (C > 1 && looped) cluster_sync_all();
+}
+
+// ------------------------------------------------------------------ host side ------
+
+template <bool PEN, bool DL, bool DEBUG>
+void* kernel_ptr() {
+  return reinterpret_cast<void*>(&tabu_kernel<PEN, DL, DEBUG>);
+}
+
+void* pick_kernel(bool pen, bool dl, bool debug) {
+  if (debug) {
+    if (pen) return dl ? kernel_ptr<true, true, true>() : kernel_ptr<true, false, true>();
+    return dl ? kernel_ptr<false, true, true>() : kernel_ptr<false, false, true>();
+  }
+  if (pen) return dl ? kernel_ptr<true, true, false>() : kernel_ptr<true, false, false>();
+  return dl ? kernel_ptr<false, true, false>() : kernel_ptr<false, false, false>();
+}
+
+int check_sizes(const asched_instance* inst, const asched_params* p) {
+  if (!inst || !p) return ASCHED_E_INVALID;
+  if (inst->n_loc < 1 || inst->n_types < 1 || inst->n_types > 2) return ASCHED_E_INVALID;
+  if (inst->n_vehicles < 1 || inst->n_missions < 0) return ASCHED_E_INVALID;
+  if (inst->n_vehicles > kMaxVehicles || inst->n_missions > kMaxMissions ||
+      inst->n_missions + inst->n_vehicles > kMaxNodes)
+    return ASCHED_E_TOO_LARGE;
+  if (inst->duty_cap < 0 || inst->horizon < 0) return ASCHED_E_INVALID;
+  if (p->tenure < 0 || p->iterations < 0 || p->lambda < 0) return ASCHED_E_INVALID;
+  if (p->cap_mode != ASCHED_HARD && p->cap_mode != ASCHED_PENALTY) return ASCHED_E_INVALID;
+  if (p->cluster_size != 0 && p->cluster_size != 1 && p->cluster_size != 2 && p->cluster_size != 4 &&
+      p->cluster_size != 8 && p->cluster_size != 16)
+    return ASCHED_E_INVALID;
+  if (p->block_threads != 0 && (p->block_threads < 64 || p->block_threads > 1024 || p->block_threads % 32))
+    return ASCHED_E_INVALID;
+  if (p->timeout_ns < 0 || p->flags != 0) return ASCHED_E_INVALID;
+  return ASCHED_OK;
+}
+
+int64_t moves_of(int64_t M, int64_t V) { return M * (M + V - 2) + M * (M - 1) / 2; }
+
+int max_smem_optin() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return -1;
+  return v;
+}
+
+// Pick block size and cluster size; returns status.
+int make_plan(const asched_instance* inst, const asched_params* p, asched_plan_t* plan, Layout* lay_out) {
+  int rc = check_sizes(inst, p);
+  if (rc != ASCHED_OK) return rc;
+  const int M = inst->n_missions, V = inst->n_vehicles;
+  const Layout lay = make_layout(M, V, inst->n_loc, inst->n_types);
+  const int64_t bytes = static_cast<int64_t>(lay.total) * 4;
+  const int limit = max_smem_optin();
+  if (limit < 0) return ASCHED_E_CUDA;
+  if (bytes > limit) return ASCHED_E_TOO_LARGE;
+  const int64_t items = static_cast<int64_t>(M + V) * M + static_cast<int64_t>(M) * (M - 1) / 2;
+  int threads = p->block_threads;
+  if (threads == 0) {
+    const int64_t want = items > M + V ? items : M + V;
+    threads = want >= 1024 ? 1024 : (want <= 64 ? 64 : round_up(static_cast<int>(want), 32));
+  }
+  int cl = p->cluster_size;
+  if (cl == 0) {
+    cl = 1;
+    while (cl < kMaxCluster && items > static_cast<int64_t>(cl) * threads) cl *= 2;
+  }
+  plan->cluster_size = cl;
+  plan->block_threads = threads;
+  plan->smem_bytes = static_cast<int32_t>(bytes);
+  plan->moves_per_iteration = moves_of(M, V);
+  if (lay_out) *lay_out = lay;
+  return ASCHED_OK;
+}
+
+int launch(const asched_instance* inst, const asched_params* p, bool debug, KParams kp, void* stream) {
+  asched_plan_t plan;
+  Layout lay;
+  int rc = make_plan(inst, p, &plan, &lay);
+  if (rc != ASCHED_OK) return rc;
+  if (!inst->travel || !inst->veh_base) return ASCHED_E_INVALID;
+  if (inst->n_missions > 0 && (!inst->pickup || !inst->delivery)) return ASCHED_E_INVALID;
+  const bool pen = p->cap_mode == ASCHED_PENALTY;
+  const bool dl = inst->deadline != nullptr;
+  void* fn = pick_kernel(pen, dl, debug);
+  kp.travel = inst->travel;
+  kp.veh_base = inst->veh_base;
+  kp.veh_type = inst->veh_type;
+  kp.pickup = inst->pickup;
+  kp.delivery = inst->delivery;
+  kp.heli_only = inst->heli_only;
+  kp.deadline = inst->deadline;
+  kp.L = inst->n_loc;
+  kp.nt = inst->n_types;
+  kp.V = inst->n_vehicles;
+  kp.M = inst->n_missions;
+  kp.cap = inst->duty_cap;
+  kp.horizon = inst->horizon;
+  kp.tenure = p->tenure;
+  kp.iterations = p->iterations;
+  kp.lambda = pen ? p->lambda : 0;
+  kp.cluster = plan.cluster_size;
+  kp.timeout_ns = p->timeout_ns > 0 ? p->timeout_ns : kDefaultTimeoutNs;
+  kp.lay = lay;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.smem_bytes) != cudaSuccess)
+    return ASCHED_E_CUDA;
+  if (plan.cluster_size > 8 &&
+      cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    return ASCHED_E_CUDA;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(plan.cluster_size, 1, 1);
+  cfg.blockDim = dim3(plan.block_threads, 1, 1);
+  cfg.dynamicSmemBytes = static_cast<size_t>(plan.smem_bytes);
+  cfg.stream = static_cast<cudaStream_t>(stream);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = plan.cluster_size;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (p->cluster_size == 0) {
+    // Automatic shape: shrink the cluster until the device can place one.
+    while (kp.cluster > 1) {
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) == cudaSuccess && n > 0) break;
+      (void)cudaGetLastError();
+      kp.cluster /= 2;
+      cfg.gridDim = dim3(kp.cluster, 1, 1);
+      attr[0].val.clusterDim.x = kp.cluster;
+    }
+  }
+  void* args[] = {&kp};
+  if (cudaLaunchKernelExC(&cfg, fn, args) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return ASCHED_E_CUDA;
+  }
+  return ASCHED_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI ----------
+
+extern "C" {
+
+int asched_abi_version(void) { return ASCHED_ABI_VERSION; }
+
+const char* asched_status_string(int status) {
+  switch (status) {
+    case ASCHED_OK: return "ok";
+    case ASCHED_E_INVALID: return "invalid argument or instance data";
+    case ASCHED_E_TOO_LARGE: return "instance too large for the on-chip layout";
+    case ASCHED_E_OVERFLOW_GUARD: return "int32 objective could overflow";
+    case ASCHED_E_INFEASIBLE_INIT: return "no feasible initial schedule";
+    case ASCHED_E_TIMEOUT: return "a bounded device wait timed out";
+    case ASCHED_E_CUDA: return "CUDA runtime error";
+    default: return "unknown status";
+  }
+}
+
+int asched_num_moves(int32_t n_missions, int32_t n_vehicles, int64_t* out) {
+  if (!out || n_missions < 0 || n_vehicles < 1) return ASCHED_E_INVALID;
+  *out = moves_of(n_missions, n_vehicles);
+  return ASCHED_OK;
+}
+
+int asched_check_instance_host(const asched_instance* inst, const asched_params* p) {
+  int rc = check_sizes(inst, p);
+  if (rc != ASCHED_OK) return rc;
+  const int L = inst->n_loc, V = inst->n_vehicles, M = inst->n_missions, nt = inst->n_types;
+  if (!inst->travel || !inst->veh_base || (M > 0 && (!inst->pickup || !inst->delivery))) return ASCHED_E_INVALID;
+  int64_t maxT = 0;
+  for (int64_t i = 0; i < static_cast<int64_t>(nt) * L * L; ++i) {
+    if (inst->travel[i] < 0) return ASCHED_E_INVALID;
+    if (inst->travel[i] > maxT) maxT = inst->travel[i];
+  }
+  for (int v = 0; v < V; ++v) {
+    if (inst->veh_base[v] < 0 || inst->veh_base[v] >= L) return ASCHED_E_INVALID;
+    const int ty = inst->veh_type ? inst->veh_type[v] : 0;
+    if (ty < 0 || ty >= nt) return ASCHED_E_INVALID;
+  }
+  for (int m = 0; m < M; ++m) {
+    const int pk = inst->pickup[m], d = inst->delivery[m];
+    if (pk < 0 || pk >= L || d < 0 || d >= L || pk == d) return ASCHED_E_INVALID;
+    if (inst->heli_only && (inst->heli_only[m] < 0 || inst->heli_only[m] > 1)) return ASCHED_E_INVALID;
+  }
+  const double lam = p->cap_mode == ASCHED_PENALTY ? static_cast<double>(p->lambda) : 0.0;
+  const double bound = 2.0 * (2.0 * M + V + 2.0) * static_cast<double>(maxT) * (1.0 + lam);
+  if (!(bound < 2147483648.0)) return ASCHED_E_OVERFLOW_GUARD;
+  return ASCHED_OK;
+}
+
+int asched_plan(const asched_instance* inst, const asched_params* params, asched_plan_t* out) {
+  if (!out) return ASCHED_E_INVALID;
+  return make_plan(inst, params, out, nullptr);
+}
+
+int asched_solve(const asched_instance* inst, const asched_params* params, const int32_t* init_route_off,
+                 const int32_t* init_route, const asched_result* out, void* stream) {
+  if (!out || !out->route_off || !out->route || !out->info) return ASCHED_E_INVALID;
+  if ((init_route_off == nullptr) != (init_route == nullptr)) return ASCHED_E_INVALID;
+  KParams kp = {};
+  kp.init_off = init_route_off;
+  kp.init_route = init_route;
+  kp.out_off = out->route_off;
+  kp.out_route = out->route;
+  kp.out_flight = out->flight;
+  kp.out_over = out->overflow;
+  kp.info = out->info;
+  kp.traj_move = out->traj_move;
+  kp.traj_z = out->traj_z;
+  return launch(inst, params, false, kp, stream);
+}
+
+int asched_eval_neighbourhood(const asched_instance* inst, const asched_params* params,
+                              const int32_t* route_off, const int32_t* route, const int32_t* tabu_until,
+                              int32_t it, int32_t z_best, int32_t* delta_out, uint8_t* flags_out,
+                              uint32_t* id_out, unsigned long long* best_key_out, int32_t* info,
+                              void* stream) {
+  if (!route_off || !route || !delta_out || !flags_out || !best_key_out || !info) return ASCHED_E_INVALID;
+  KParams kp = {};
+  kp.init_off = route_off;
+  kp.init_route = route;
+  kp.tabu_in = tabu_until;
+  kp.dbg_it = it;
+  kp.dbg_zbest = z_best;
+  kp.dbg_delta = delta_out;
+  kp.dbg_flags = flags_out;
+  kp.dbg_id = id_out;
+  kp.dbg_key = best_key_out;
+  kp.info = info;
+  return launch(inst, params, true, kp, stream);
+}
+
+}  // extern "C"

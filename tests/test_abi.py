@@ -1,0 +1,97 @@
+"""The C ABI library builds, loads and exports every declared entry point; host-side
+logic (sizes, validation of host data, status strings) works without a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2002_11710_gb300 import _lib, api, gen
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "asched.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(asched_\w+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = _lib.load()
+    names = declared_functions()
+    assert names, "no declarations found"
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(_lib.SIGNATURES), "binding and header disagree"
+
+
+def test_abi_version_and_status_strings():
+    L = _lib.load()
+    assert L.asched_abi_version() == 1
+    for rc in (0, -1, -2, -3, -4, -5, -6, -99):
+        assert isinstance(_lib.status_string(rc), str)
+    assert _lib.status_string(0) == "ok"
+
+
+def test_num_moves_closed_form():
+    for M in range(0, 40, 7):
+        for V in (1, 2, 5, 20):
+            assert api.num_moves(M, V) == M * (M + V - 2) + M * (M - 1) // 2
+    assert api.num_moves(100, 20) == 16750
+    with pytest.raises(api.AschedError):
+        api.num_moves(-1, 3)
+
+
+def _params(**kw):
+    return api.make_params(**{**dict(tenure=5, iterations=10, cap_mode=gen.PENALTY, lam=1000), **kw})
+
+
+def test_check_instance_host_accepts_the_workloads():
+    for inst in (gen.tiny(0), gen.paper_shaped(0), gen.large(0), gen.paper_model(1, 20)):
+        assert api.check_instance_host(inst, _params()) == api.OK
+
+
+def test_check_instance_host_rejects_bad_data():
+    base = gen.random_instance(5, n_loc=6, n_vehicles=3, n_missions=8)
+
+    def variant(**kw):
+        return gen.Instance(**{**base.__dict__, **kw})
+
+    p = base.pickup.copy(); p[2] = 6
+    assert api.check_instance_host(variant(pickup=p), _params()) == api.E_INVALID
+    d = base.delivery.copy(); d[1] = base.pickup[1]
+    assert api.check_instance_host(variant(delivery=d), _params()) == api.E_INVALID
+    t = base.travel.copy(); t[0, 1, 2] = -1
+    assert api.check_instance_host(variant(travel=t), _params()) == api.E_INVALID
+    vb = base.veh_base.copy(); vb[0] = -3
+    assert api.check_instance_host(variant(veh_base=vb), _params()) == api.E_INVALID
+    vt = base.veh_type.copy(); vt[0] = 1  # only one travel layer
+    assert api.check_instance_host(variant(veh_type=vt), _params()) == api.E_INVALID
+    h = np.zeros(8, np.int32); h[0] = 2
+    assert api.check_instance_host(variant(heli_only=h), _params()) == api.E_INVALID
+    big = variant(travel=base.travel * 100000)
+    assert api.check_instance_host(big, _params()) == api.E_OVERFLOW_GUARD
+    assert api.check_instance_host(big, _params(cap_mode=gen.HARD)) == api.OK
+
+
+def test_check_instance_host_rejects_bad_params():
+    inst = gen.tiny(0)
+    assert api.check_instance_host(inst, _params(cap_mode=3)) == api.E_INVALID
+    assert api.check_instance_host(inst, _params(tenure=-1)) == api.E_INVALID
+    assert api.check_instance_host(inst, _params(cluster_size=5)) == api.E_INVALID
+    assert api.check_instance_host(inst, _params(block_threads=100)) == api.E_INVALID
+    assert api.check_instance_host(inst, _params(block_threads=2048)) == api.E_INVALID
+    assert api.check_instance_host(inst, _params(cluster_size=16, block_threads=64)) == api.OK
+
+
+def test_plan_without_a_device_reports_cuda_error():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    inst = gen.tiny(0)
+    s, keep = api.host_struct(inst)
+    out = _lib.Plan()
+    rc = _lib.load().asched_plan(ctypes.byref(s), ctypes.byref(_params()), ctypes.byref(out))
+    assert rc == api.E_CUDA
