@@ -114,7 +114,7 @@ typedef struct {
  *   cluster_size        CTAs cooperating on one instance (a thread-block cluster):
  *                       0 = automatic, else 1, 2, 4, 8 or 16. Results do not depend
  *                       on it.
- *   block_threads       0 = automatic, else a multiple of 32 in [64, 1024].
+ *   block_threads       0 = automatic, else a multiple of 32 in [64, 512].
  *   timeout_ns          bound on every wait between CTAs; 0 = 1 s.
  *   flags               must be 0. */
 typedef struct {

@@ -12,7 +12,8 @@
 //     cluster of C CTAs (C = 1..16), one CTA per SM. Each CTA holds a complete copy
 //     of the instance and of the search state in shared memory and applies every
 //     move itself, so the only traffic between CTAs per iteration is one 64-bit key
-//     per CTA (DSMEM store + remote mbarrier arrive, bounded wait).
+//     per CTA (a relaxed DSMEM store of a key tagged with the iteration, polled by
+//     the receivers with a bounded wait).
 //   * Shared memory holds two node-by-mission gather tables built once per launch:
 //       A[t][l][m] = T_t[l][p_m] + T_t[p_m][d_m]   (fly from location l to m's pickup, then m)
 //       B[t][l][m] = T_t[d_m][l]                   (from m's delivery to location l)
@@ -40,6 +41,7 @@ constexpr uint32_t kSwapBit = 0x80000000u;
 constexpr uint32_t kNullMove = 0xFFFFFFFFu;
 constexpr uint64_t kNoKey = ~0ull;
 constexpr int kMaxCluster = 16;
+constexpr int kMaxThreads = 512;  // per CTA; leaves 128 registers per thread
 constexpr int kIdShift = 13;
 constexpr uint32_t kIdMask = (1u << kIdShift) - 1u;
 constexpr int kMaxMissions = 4095;
@@ -49,16 +51,19 @@ constexpr int64_t kDefaultTimeoutNs = 1000000000ll;
 
 // ------------------------------------------------------------------ layout ---------
 
-constexpr int kStateArrays = 17;
-enum {
-  ST_NXT = 0, ST_PRV, ST_VEHP, ST_ROWA, ST_ROWB, ST_ROWBN, ST_ROWE, ST_INLEG, ST_REM,
-  ST_SLOT, ST_FBP, ST_SRCP, ST_DEPX, ST_YLIM, ST_YLIMN, ST_REMOK, ST_FL
-};
+// Per-node records (one buffer). A node word packs the next node and the node's
+// vehicle word: nv = next | vw << 13, vw = vehicle | plane << 10 | heli-only << 11.
+//   R2[t] = {nv, removal delta}                       relocation, mission side
+//   Y4[t] = {A row of prev(t), B row of t, leg prev(t) -> t, nv}   relocation, gap side
+//   S4[t] = {nv, A row of prev(t), B row of next(t), slot cost}    swap side
+//   D4[t] = {dep(prev t), arrive-by slack at t, slack at next(t), removal link ok}
+//   PRV[t] previous node; FB[v] flight of vehicle v minus the duty cap.
+constexpr int kBufWordsPerNode = 15;
 
 struct Layout {  // offsets in int32 words from the start of dynamic shared memory
-  int A, B, tabu, cmat, wm, heli, eloc, sloc, vtype, st0, st1, best, order, cnt, gend,
-      gdep, gfl, glast, misc, warpkey, slots, mbar, total;
-  int Mp, Np, Vp;
+  int A, B, tabu, cmat, wm, eloc, sloc, vtype, tyl, tym, st0, st1, best, order, cnt, gend, gdep, gfl,
+      glast, misc, warpkey, slots, total;
+  int Mp, Np, Vp, buf;
 };
 
 __host__ __device__ inline int round_up(int x, int k) { return (x + k - 1) / k * k; }
@@ -68,18 +73,20 @@ __host__ __device__ inline Layout make_layout(int M, int V, int L, int nt) {
   y.Mp = round_up(M > 0 ? M : 1, 32);
   y.Np = round_up(M + V, 4);
   y.Vp = round_up(V, 4);
+  y.buf = kBufWordsPerNode * y.Np + y.Vp;  // R2 Y4 S4 D4 PRV, then FB
   int o = 0;
   y.A = o;       o += nt * L * y.Mp;
   y.B = o;       o += nt * L * y.Mp;
   y.tabu = o;    o += V * y.Mp;
   y.cmat = o;    o += nt * y.Mp;
   y.wm = o;      o += y.Mp;
-  y.heli = o;    o += y.Mp;
   y.eloc = o;    o += y.Np;
   y.sloc = o;    o += y.Np;
   y.vtype = o;   o += y.Vp;
-  y.st0 = o;     o += kStateArrays * y.Np;
-  y.st1 = o;     o += kStateArrays * y.Np;
+  y.tyl = o;     o += y.Vp;
+  y.tym = o;     o += y.Vp;
+  y.st0 = o;     o += y.buf;
+  y.st1 = o;     o += y.buf;
   y.best = o;    o += y.Np;
   y.order = o;   o += y.Mp;
   y.cnt = o;     o += y.Mp;
@@ -91,7 +98,6 @@ __host__ __device__ inline Layout make_layout(int M, int V, int L, int nt) {
   o = round_up(o, 4);
   y.warpkey = o; o += 2 * 32;
   y.slots = o;   o += 2 * 2 * kMaxCluster;
-  y.mbar = o;    o += 4;
   y.total = o;
   return y;
 }
@@ -144,38 +150,22 @@ __device__ __forceinline__ void cluster_sync_all() {
                    : "memory");
 }
 
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
 __device__ __forceinline__ uint32_t mapa_rank(uint32_t local_addr, uint32_t rank) {
   uint32_t r;
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_addr), "r"(rank));
   return r;
 }
 
-__device__ __forceinline__ void st_cluster_u64(uint32_t addr, uint64_t v) {
-  asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+// Store into a peer CTA's shared memory (relaxed, cluster scope).
+__device__ __forceinline__ void st_peer_u64(uint32_t cluster_addr, uint64_t v) {
+  asm volatile("st.relaxed.cluster.shared::cluster.u64 [%0], %1;" ::"r"(cluster_addr), "l"(v) : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(addr), "r"(parity)
-      : "memory");
-  return ok != 0;
+// Load from this CTA's shared memory, observing peers' relaxed stores.
+__device__ __forceinline__ uint64_t ld_own_u64(uint32_t cta_addr) {
+  uint64_t v;
+  asm volatile("ld.relaxed.cluster.shared::cta.u64 %0, [%1];" : "=l"(v) : "r"(cta_addr) : "memory");
+  return v;
 }
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -184,18 +174,15 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// Wait for the phase of `bar` with the given parity; false after timeout_ns.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int64_t timeout_ns) {
-  const uint32_t addr = smem_u32(bar);
-  if (mbar_try_wait(addr, parity)) return true;
-  const uint64_t t0 = global_ns();
-  while (true) {
-    if (mbar_try_wait(addr, parity)) return true;
-    if ((int64_t)(global_ns() - t0) > timeout_ns) return false;
-  }
-}
-
 // ------------------------------------------------------------------ keys -----------
+
+// Bits 26-29 of every move id are zero (R ids < 2^26; S ids use bit 31 and bits
+// 0-25), so keys crossing the cluster carry an iteration tag there: 8 | ((it >> 1) & 7).
+// Slots start at 0 (tag 0), and consecutive uses of a slot buffer carry different tags.
+constexpr uint64_t kTagMask = 0xFull << 26;
+__device__ __forceinline__ uint64_t iter_tag(int it) {
+  return static_cast<uint64_t>(8 | ((it >> 1) & 7)) << 26;
+}
 
 __device__ __forceinline__ uint64_t pack_key(int32_t d, uint32_t id) {
   return (static_cast<uint64_t>(static_cast<uint32_t>(d) ^ 0x80000000u) << 32) | id;
@@ -216,70 +203,62 @@ __device__ __forceinline__ int32_t pos0(int32_t x) { return x > 0 ? x : 0; }
 
 // ------------------------------------------------------------------ shared state ---
 
-// One buffer of per-node records: array i of node t is base[i * np + t].
-struct State {
-  int32_t* base;
-  int np;
-  __device__ __forceinline__ int32_t* operator[](int i) const { return base + i * np; }
+// All state lives in dynamic shared memory and is addressed as word offsets into this
+// one array, so every access compiles to a shared-memory load or store.
+extern __shared__ __align__(16) int32_t g_smem[];
+
+struct Arr {  // an int32 array in shared memory
+  int off;
+  __device__ __forceinline__ int32_t& operator[](int i) const { return g_smem[off + i]; }
+};
+
+struct State {  // one buffer of per-node records (see the layout notes)
+  int base, np;
+  __device__ __forceinline__ int2* r2() const { return reinterpret_cast<int2*>(g_smem + base); }
+  __device__ __forceinline__ int4* y4() const { return reinterpret_cast<int4*>(g_smem + base + 2 * np); }
+  __device__ __forceinline__ int4* s4() const { return reinterpret_cast<int4*>(g_smem + base + 6 * np); }
+  __device__ __forceinline__ int4* d4() const { return reinterpret_cast<int4*>(g_smem + base + 10 * np); }
+  __device__ __forceinline__ int32_t* prv() const { return g_smem + base + 14 * np; }
+  __device__ __forceinline__ int32_t* fb() const { return g_smem + base + 15 * np; }
+  __device__ __forceinline__ int32_t& nv(int t) const { return g_smem[base + 2 * t]; }
 };
 
 struct Smem {
-  int32_t* A;
-  int32_t* B;
-  int32_t* tabu;
-  int32_t* cmat;
-  int32_t* wm;
-  int32_t* heli;
-  int32_t* eloc;
-  int32_t* sloc;
-  int32_t* vtype;
-  int32_t* st_base;  // buffer 0; buffer 1 follows at st_stride words
-  int st_stride;
-  int np;
-  __device__ __forceinline__ State st(int k) const {
-    State s;
-    s.base = st_base + k * st_stride;
-    s.np = np;
-    return s;
+  Arr A, B, tabu, cmat, wm, eloc, sloc, vtype, tyl, tym, best, order, cnt, gend, gdep, gfl, glast, misc;
+  int st0, buf, np;
+  int warpkey_off, slots_off;
+  __device__ __forceinline__ State st(int k) const { return State{st0 + k * buf, np}; }
+  __device__ __forceinline__ uint64_t* warpkey() const {
+    return reinterpret_cast<uint64_t*>(g_smem + warpkey_off);
   }
-  int32_t* best;
-  int32_t* order;
-  int32_t* cnt;
-  int32_t* gend;
-  int32_t* gdep;
-  int32_t* gfl;
-  int32_t* glast;
-  int32_t* misc;
-  uint64_t* warpkey;
-  uint64_t* slots;
-  uint64_t* mbar;
+  __device__ __forceinline__ uint64_t* slots() const { return reinterpret_cast<uint64_t*>(g_smem + slots_off); }
 };
 
-__device__ inline Smem carve(int32_t* base, const Layout& y) {
+__device__ inline Smem carve(const Layout& y) {
   Smem s;
-  s.A = base + y.A;
-  s.B = base + y.B;
-  s.tabu = base + y.tabu;
-  s.cmat = base + y.cmat;
-  s.wm = base + y.wm;
-  s.heli = base + y.heli;
-  s.eloc = base + y.eloc;
-  s.sloc = base + y.sloc;
-  s.vtype = base + y.vtype;
-  s.st_base = base + y.st0;
-  s.st_stride = y.st1 - y.st0;
+  s.A = Arr{y.A};
+  s.B = Arr{y.B};
+  s.tabu = Arr{y.tabu};
+  s.cmat = Arr{y.cmat};
+  s.wm = Arr{y.wm};
+  s.eloc = Arr{y.eloc};
+  s.sloc = Arr{y.sloc};
+  s.vtype = Arr{y.vtype};
+  s.tyl = Arr{y.tyl};
+  s.tym = Arr{y.tym};
+  s.st0 = y.st0;
+  s.buf = y.buf;
   s.np = y.Np;
-  s.best = base + y.best;
-  s.order = base + y.order;
-  s.cnt = base + y.cnt;
-  s.gend = base + y.gend;
-  s.gdep = base + y.gdep;
-  s.gfl = base + y.gfl;
-  s.glast = base + y.glast;
-  s.misc = base + y.misc;
-  s.warpkey = reinterpret_cast<uint64_t*>(base + y.warpkey);
-  s.slots = reinterpret_cast<uint64_t*>(base + y.slots);
-  s.mbar = reinterpret_cast<uint64_t*>(base + y.mbar);
+  s.best = Arr{y.best};
+  s.order = Arr{y.order};
+  s.cnt = Arr{y.cnt};
+  s.gend = Arr{y.gend};
+  s.gdep = Arr{y.gdep};
+  s.gfl = Arr{y.gfl};
+  s.glast = Arr{y.glast};
+  s.misc = Arr{y.misc};
+  s.warpkey_off = y.warpkey;
+  s.slots_off = y.slots;
   return s;
 }
 
@@ -290,148 +269,174 @@ struct Ctx {  // per-launch constants every thread keeps in registers
   int M, V, N, L, Mp, cap, horizon, lam;
 };
 
-// Rewrite every record of node t in state S2 from its links (nx, pv), its vehicle
-// word vp (vehicle | plane << 16) and the flight f2 of that vehicle.
+constexpr int kNodeMask = 0x1FFF;  // next-node field of a node word
+__device__ __forceinline__ int nv_next(int nv) { return nv & kNodeMask; }
+__device__ __forceinline__ int nv_vw(int nv) { return (nv >> 13) & 0xFFF; }
+__device__ __forceinline__ int nv_veh(int nv) { return (nv >> 13) & 0x3FF; }
+__device__ __forceinline__ int vw_veh(int vw) { return vw & 0x3FF; }
+__device__ __forceinline__ int vw_plane(int vw) { return (vw >> 10) & 1; }
+// the vehicle part of `from` with the heli-only bit of `own`
+__device__ __forceinline__ int vw_move(int from, int own) { return (from & 0x7FF) | (own & 0x800); }
+
+// Write every record of node t into buffer S2 from its links (nx, pv), its vehicle
+// word vw and the flight f2 of that vehicle.
 template <bool PEN, bool DL>
 __device__ __forceinline__ void write_records(const Smem& sm, const State& S2, const Ctx& c, int t,
-                                              int nx, int pv, int vp, int f2) {
-  const int vv = vp & 0xFFFF;
-  const int ty = sm.vtype[vv];
-  const int lb = ty * c.L;
-  const int rowA = (lb + sm.eloc[pv]) * c.Mp;
-  const int rowB = (lb + sm.sloc[t]) * c.Mp;
-  S2[ST_NXT][t] = nx;
-  S2[ST_PRV][t] = pv;
-  S2[ST_VEHP][t] = vp;
-  S2[ST_ROWA][t] = rowA;
-  S2[ST_ROWB][t] = rowB;
-  S2[ST_FBP][t] = f2 - c.cap;
-  if (DL) S2[ST_DEPX][t] = pv < c.M ? sm.wm[pv] : 0;
+                                              int nx, int pv, int vw, int f2) {
+  const int plane = vw_plane(vw);
+  const int tyl = plane * c.L, tym = plane * c.Mp;
+  const int rowA = (tyl + sm.eloc[pv]) * c.Mp;
+  const int rowB = (tyl + sm.sloc[t]) * c.Mp;
+  const int nv = nx | (vw << 13);
+  const int dep = (DL && pv < c.M) ? sm.wm[pv] : 0;
+  S2.prv()[t] = pv;
   if (t < c.M) {
-    const int rowBn = (lb + sm.sloc[nx]) * c.Mp;
-    const int rowE = (lb + sm.eloc[t]) * c.Mp;
+    const int rowBn = (tyl + sm.sloc[nx]) * c.Mp;
     const int aT = sm.A[rowA + t];
     const int bT = sm.B[rowBn + t];
     const int slot = aT + bT;
-    const int* cm = sm.cmat + ty * c.Mp;
-    const int ct = cm[t];
-    const int leg = nx < c.M ? sm.A[rowA + nx] - cm[nx] : (pv < c.M ? sm.B[rowBn + pv] : 0);
-    const int rem = leg - slot;
-    const int fb = f2 - c.cap;
-    S2[ST_ROWBN][t] = rowBn;
-    S2[ST_ROWE][t] = rowE;
-    S2[ST_SLOT][t] = slot;
-    S2[ST_REM][t] = rem;
-    S2[ST_INLEG][t] = aT - ct;
-    S2[ST_SRCP][t] = PEN ? pos0(fb + rem) - pos0(fb) : fb + rem;
+    const int ct = sm.cmat[tym + t];
+    const int cn = nx < c.M ? sm.cmat[tym + nx] : 0;
+    const int leg = nx < c.M ? sm.A[rowA + nx] - cn : (pv < c.M ? sm.B[rowBn + pv] : 0);
+    S2.r2()[t] = make_int2(nv, leg - slot);
+    S2.y4()[t] = make_int4(rowA, rowB, aT - ct, nv);
+    S2.s4()[t] = make_int4(nv, rowA, rowBn, slot);
     if (DL) {
-      const int dep = pv < c.M ? sm.wm[pv] : 0;
-      S2[ST_YLIM][t] = sm.wm[t] - ct;
-      S2[ST_YLIMN][t] = nx < c.M ? sm.wm[nx] - cm[nx] : c.horizon;
-      const int lim = nx < c.M ? sm.wm[nx] : c.horizon;
-      const int add = nx < c.M ? cm[nx] : 0;
-      S2[ST_REMOK][t] = (dep + leg + add <= lim) ? 1 : 0;
+      const int wn = nx < c.M ? sm.wm[nx] : c.horizon;
+      S2.d4()[t] = make_int4(dep, sm.wm[t] - ct, wn - cn, (dep + leg + cn <= wn) ? 1 : 0);
     }
   } else {
-    S2[ST_INLEG][t] = (pv == t) ? 0 : sm.B[rowB + pv];
-    if (DL) S2[ST_YLIM][t] = c.horizon;
+    const int inleg = (pv == t) ? 0 : sm.B[rowB + pv];
+    S2.r2()[t] = make_int2(nv, 0);
+    S2.y4()[t] = make_int4(rowA, rowB, inleg, nv);
+    S2.s4()[t] = make_int4(nv, 0, 0, 0);
+    S2.fb()[t - c.M] = f2 - c.cap;
+    if (DL) S2.d4()[t] = make_int4(dep, c.horizon, 0, 1);
   }
 }
 
-// Relocation R(m, y): take m out, put it immediately before node y.
+__device__ __forceinline__ uint8_t move_flags(bool feas, bool tabu, bool asp, bool adm) {
+  return static_cast<uint8_t>((feas ? 1 : 0) | (tabu ? 2 : 0) | (asp ? 4 : 0) | (adm ? 8 : 0));
+}
+
+// Relocation R(m, y): take m out, put it immediately before node y. The inputs are
+// already loaded: m's node word and removal delta, the gap record g of y, the table
+// entries a = A[row of prev(y)][m], b = B[row of y][m], y's vehicle slack fy and the
+// tabu stamp of (m, vehicle of y).
 template <bool PEN, bool DL, bool DEBUG>
-__device__ __forceinline__ uint64_t eval_relocate(const Smem& sm, const State& S, const Ctx& c, int y,
-                                                  int m, int it, int Z, int zbest, const KParams& P) {
-  const int s_m = S[ST_NXT][m];
-  if (y == m || y == s_m) return kNoKey;
-  const int vpy = S[ST_VEHP][y], vpm = S[ST_VEHP][m];
-  const int vy = vpy & 0xFFFF, vm = vpm & 0xFFFF;
-  const int a = sm.A[S[ST_ROWA][y] + m];
-  const int b = sm.B[S[ST_ROWB][y] + m];
-  const int ins = a + b - S[ST_INLEG][y];
-  const int rem = S[ST_REM][m];
-  const int fy = S[ST_FBP][y];
+__device__ __forceinline__ uint64_t reloc_one(const Smem& sm, const State& S, const Ctx& c, int y, int m,
+                                              int nvm, int rem, const int4& g, int a, int b, int fy,
+                                              int stamp, int it, int Z, int zbest, const KParams& P) {
+  const bool valid = (y != m) && (y != nv_next(nvm));
+  const int vm = nv_veh(nvm), vy = nv_veh(g.w);
+  const int ins = a + b - g.z;
+  const int d = rem + ins;
+  // Same route: one flight changes by d. Different routes: the source by rem, the
+  // target by ins. Both are computed and selected, so lanes never diverge.
+  const int fm = S.fb()[vm];
+  const bool same = vm == vy;
   int delta;
   bool feas;
-  if (vm == vy) {
-    const int d = rem + ins;
-    if (PEN) {
-      delta = d + c.lam * (pos0(fy + d) - pos0(fy));
-      feas = true;
-    } else {
-      delta = d;
-      feas = fy + d <= 0;
-    }
+  if (PEN) {
+    const int pen = same ? pos0(fy + d) : pos0(fm + rem) - pos0(fm) + pos0(fy + ins);
+    delta = d + c.lam * (pen - pos0(fy));
+    feas = true;
   } else {
-    const int sp = S[ST_SRCP][m];
-    if (PEN) {
-      delta = rem + ins + c.lam * (sp + pos0(fy + ins) - pos0(fy));
-      feas = true;
-    } else {
-      delta = rem + ins;
-      feas = (sp <= 0) && (fy + ins <= 0);
-    }
+    delta = d;
+    feas = same ? (fy + d <= 0) : ((fm + rem <= 0) && (fy + ins <= 0));
   }
-  feas = feas && !(sm.heli[m] && (vpy >> 16));
+  feas = feas && !((nvm >> 24) & (g.w >> 23) & 1);  // heli-only m onto a plane
   if (DL) {
+    const int4 dy = S.d4()[y];
     const int w = sm.wm[m];
-    feas = feas && (S[ST_DEPX][y] + a <= w) && (w + b <= S[ST_YLIM][y]) && S[ST_REMOK][m];
+    feas = feas && (dy.x + a <= w) && (w + b <= dy.y) && S.d4()[m].w;
   }
-  const bool tabu = sm.tabu[vy * c.Mp + m] >= it;
+  const bool tabu = stamp >= it;
   const bool asp = Z + delta < zbest;
-  const bool adm = feas && (!tabu || asp);
+  const bool adm = valid && feas && (!tabu || asp);
   const uint32_t id = (static_cast<uint32_t>(m) << kIdShift) | static_cast<uint32_t>(y);
-  if (DEBUG) {
-    const int64_t idx = static_cast<int64_t>(m) * (c.N - 2) + y - (y > m) - (y > s_m);
+  if (DEBUG && valid) {
+    const int64_t idx = static_cast<int64_t>(m) * (c.N - 2) + y - (y > m) - (y > nv_next(nvm));
     P.dbg_delta[idx] = delta;
-    P.dbg_flags[idx] = static_cast<uint8_t>((feas ? 1 : 0) | (tabu ? 2 : 0) | (asp ? 4 : 0) | (adm ? 8 : 0));
+    P.dbg_flags[idx] = move_flags(feas, tabu, asp, adm);
     if (P.dbg_id) P.dbg_id[idx] = id;
   }
   return adm ? pack_key(delta, id) : kNoKey;
+}
+
+// Relocations of the mission pair (m0, m0 + 1), m0 even, before node y: every load
+// serves both (64-bit loads of consecutive table and record entries).
+template <bool PEN, bool DL, bool DEBUG>
+__device__ __forceinline__ uint64_t eval_relocate_pair(const Smem& sm, const State& S, const Ctx& c,
+                                                       int y, int m0, int it, int Z, int zbest,
+                                                       const KParams& P) {
+  const int4 rr = *reinterpret_cast<const int4*>(S.r2() + m0);  // {nv, rem} of m0 and m0 + 1
+  const int4 g = S.y4()[y];  // A row, B row, leg into y, node word of y
+  const int vy = nv_veh(g.w);
+  const int2 a2 = *reinterpret_cast<const int2*>(&sm.A[g.x + m0]);
+  const int2 b2 = *reinterpret_cast<const int2*>(&sm.B[g.y + m0]);
+  const int2 st = *reinterpret_cast<const int2*>(&sm.tabu[vy * c.Mp + m0]);
+  const int fy = S.fb()[vy];
+  uint64_t k = reloc_one<PEN, DL, DEBUG>(sm, S, c, y, m0, rr.x, rr.y, g, a2.x, b2.x, fy, st.x, it, Z, zbest, P);
+  if (m0 + 1 < c.M)
+    k = min_u64(k, reloc_one<PEN, DL, DEBUG>(sm, S, c, y, m0 + 1, rr.z, rr.w, g, a2.y, b2.y, fy, st.y, it, Z,
+                                             zbest, P));
+  return k;
+}
+
+// Cost parts of swap S(a, b): t1..t4 as in the design notes, adjacency-aware.
+struct SwapParts {
+  int4 sa, sb;
+  int t1, t2, t3, t4;
+  bool adjA, adjB;
+};
+
+__device__ __forceinline__ SwapParts swap_parts(const Smem& sm, const State& S, const Ctx& c, int a, int b) {
+  SwapParts q;
+  q.sa = S.s4()[a];
+  q.sb = S.s4()[b];
+  q.adjA = nv_next(q.sa.x) == b;  // a immediately before b
+  q.adjB = nv_next(q.sb.x) == a;  // b immediately before a
+  // A row of a mission's own delivery (needed only next to the other mission)
+  const int rowEa = q.adjB ? (vw_plane(nv_vw(q.sa.x)) * c.L + sm.eloc[a]) * c.Mp : 0;
+  const int rowEb = q.adjA ? (vw_plane(nv_vw(q.sb.x)) * c.L + sm.eloc[b]) * c.Mp : 0;
+  q.t1 = sm.A[(q.adjB ? rowEa : q.sa.y) + b];
+  q.t2 = sm.B[q.sa.z + (q.adjA ? a : b)];
+  q.t3 = sm.A[(q.adjA ? rowEb : q.sb.y) + a];
+  q.t4 = sm.B[q.sb.z + (q.adjB ? b : a)];
+  return q;
 }
 
 // Swap S(a, b): the two missions exchange places.
 template <bool PEN, bool DL, bool DEBUG>
 __device__ __forceinline__ uint64_t eval_swap(const Smem& sm, const State& S, const Ctx& c, int a, int b,
                                               int it, int Z, int zbest, const KParams& P) {
-  const int vpa = S[ST_VEHP][a], vpb = S[ST_VEHP][b];
-  const int va = vpa & 0xFFFF, vb = vpb & 0xFFFF;
-  const int na = S[ST_NXT][a], nb = S[ST_NXT][b];
-  const bool adjA = (na == b), adjB = (nb == a);
-  const int t1 = sm.A[(adjB ? S[ST_ROWE][a] : S[ST_ROWA][a]) + b];
-  const int t2 = sm.B[S[ST_ROWBN][a] + (adjA ? a : b)];
-  const int t3 = sm.A[(adjA ? S[ST_ROWE][b] : S[ST_ROWA][b]) + a];
-  const int t4 = sm.B[S[ST_ROWBN][b] + (adjB ? b : a)];
-  const int da = t1 + t2 - S[ST_SLOT][a];
-  const int db = t3 + t4 - S[ST_SLOT][b];
-  const int fa = S[ST_FBP][a], fb = S[ST_FBP][b];
+  const SwapParts q = swap_parts(sm, S, c, a, b);
+  const int nva = q.sa.x, nvb = q.sb.x;
+  const int va = nv_veh(nva), vb = nv_veh(nvb);
+  const int da = q.t1 + q.t2 - q.sa.w;
+  const int db = q.t3 + q.t4 - q.sb.w;
+  const int fa = S.fb()[va], fb = S.fb()[vb];
+  const bool same = va == vb;
+  const int d = da + db;
   int delta;
   bool feas;
-  if (va == vb) {
-    const int d = da + db;
-    if (PEN) {
-      delta = d + c.lam * (pos0(fa + d) - pos0(fa));
-      feas = true;
-    } else {
-      delta = d;
-      feas = fa + d <= 0;
-    }
+  if (PEN) {
+    const int pen = same ? pos0(fa + d) - pos0(fa) : pos0(fa + da) - pos0(fa) + pos0(fb + db) - pos0(fb);
+    delta = d + c.lam * pen;
+    feas = true;
   } else {
-    if (PEN) {
-      delta = da + db + c.lam * (pos0(fa + da) - pos0(fa) + pos0(fb + db) - pos0(fb));
-      feas = true;
-    } else {
-      delta = da + db;
-      feas = (fa + da <= 0) && (fb + db <= 0);
-    }
+    delta = d;
+    feas = same ? (fa + d <= 0) : ((fa + da <= 0) && (fb + db <= 0));
   }
-  feas = feas && !((sm.heli[a] && (vpb >> 16)) || (sm.heli[b] && (vpa >> 16)));
+  feas = feas && !((((nva >> 24) & (nvb >> 23)) | ((nvb >> 24) & (nva >> 23))) & 1);
   if (DL) {
+    const int4 xa = S.d4()[a], xb = S.d4()[b];
     const int wa = sm.wm[a], wb = sm.wm[b];
-    const bool l1 = (adjB ? wa : S[ST_DEPX][a]) + t1 <= wb;
-    const bool l2 = adjA || (wb + t2 <= S[ST_YLIMN][a]);
-    const bool l3 = (adjA ? wb : S[ST_DEPX][b]) + t3 <= wa;
-    const bool l4 = adjB || (wa + t4 <= S[ST_YLIMN][b]);
+    const bool l1 = (q.adjB ? wa : xa.x) + q.t1 <= wb;
+    const bool l2 = q.adjA || (wb + q.t2 <= xa.z);
+    const bool l3 = (q.adjA ? wb : xb.x) + q.t3 <= wa;
+    const bool l4 = q.adjB || (wa + q.t4 <= xb.z);
     feas = feas && l1 && l2 && l3 && l4;
   }
   const bool tabu = (sm.tabu[vb * c.Mp + a] >= it) || (sm.tabu[va * c.Mp + b] >= it);
@@ -443,7 +448,7 @@ __device__ __forceinline__ uint64_t eval_swap(const Smem& sm, const State& S, co
     const int64_t rtot = static_cast<int64_t>(c.M) * (c.N - 2);
     const int64_t idx = rtot + static_cast<int64_t>(m1) * (2 * c.M - m1 - 1) / 2 + (m2 - m1 - 1);
     P.dbg_delta[idx] = delta;
-    P.dbg_flags[idx] = static_cast<uint8_t>((feas ? 1 : 0) | (tabu ? 2 : 0) | (asp ? 4 : 0) | (adm ? 8 : 0));
+    P.dbg_flags[idx] = move_flags(feas, tabu, asp, adm);
     if (P.dbg_id) P.dbg_id[idx] = id;
   }
   return adm ? pack_key(delta, id) : kNoKey;
@@ -452,9 +457,8 @@ __device__ __forceinline__ uint64_t eval_swap(const Smem& sm, const State& S, co
 // ------------------------------------------------------------------ the kernel -----
 
 template <bool PEN, bool DL, bool DEBUG>
-__global__ void __launch_bounds__(1024, 1) tabu_kernel(const __grid_constant__ KParams P) {
-  extern __shared__ __align__(16) int32_t smem_raw[];
-  const Smem sm = carve(smem_raw, P.lay);
+__global__ void __launch_bounds__(kMaxThreads, 1) tabu_kernel(const __grid_constant__ KParams P) {
+  const Smem sm = carve(P.lay);
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
   const int C = P.cluster;
@@ -481,13 +485,11 @@ __global__ void __launch_bounds__(1024, 1) tabu_kernel(const __grid_constant__ K
       const int h = P.heli_only ? P.heli_only[i] : 0;
       bad |= (p < 0) | (p >= L) | (d < 0) | (d >= L) | (p == d) | (h < 0) | (h > 1);
       sm.wm[i] = P.deadline ? P.deadline[i] : 0;
-      sm.heli[i] = h;
       sm.eloc[i] = d;
       sm.sloc[i] = p;
       sm.cnt[i] = 0;
     } else {
       sm.wm[i] = 0;
-      sm.heli[i] = 0;
     }
   }
   for (int v = tid; v < V; v += nthr) {
@@ -497,6 +499,8 @@ __global__ void __launch_bounds__(1024, 1) tabu_kernel(const __grid_constant__ K
     sm.eloc[M + v] = b;
     sm.sloc[M + v] = b;
     sm.vtype[v] = ty;
+    sm.tyl[v] = ty * L;
+    sm.tym[v] = ty * Mp;
   }
   int maxT = 0;
   for (int i = tid; i < nt * L * L; i += nthr) {
@@ -514,7 +518,8 @@ __global__ void __launch_bounds__(1024, 1) tabu_kernel(const __grid_constant__ K
     if (!(bound < 2147483648.0)) status = ASCHED_E_OVERFLOW_GUARD;
   }
 
-  // ---- prologue 2: gather tables, in-mission legs, tabu stamps
+  // ---- prologue 2: gather tables, in-mission legs, tabu stamps, route ends
+  const State S0 = sm.st(0);
   if (status == ASCHED_OK) {
     for (int i = tid; i < nt * L * Mp; i += nthr) {
       const int r = i / Mp, m = i - r * Mp;
@@ -542,19 +547,15 @@ __global__ void __launch_bounds__(1024, 1) tabu_kernel(const __grid_constant__ K
       const int v = i / Mp, m = i - v * Mp;
       sm.tabu[i] = (P.tabu_in && m < M) ? P.tabu_in[static_cast<int64_t>(m) * V + v] : -1;
     }
-    // links of route ends; vehicle words
-    const State S0 = sm.st(0);
     for (int v = tid; v < V; v += nthr) {
-      S0[ST_NXT][M + v] = M + v;
-      S0[ST_PRV][M + v] = M + v;
-      S0[ST_VEHP][M + v] = v | ((sm.vtype[v] != 0 ? 1 : 0) << 16);
+      S0.nv(M + v) = (M + v) | ((v | ((sm.vtype[v] != 0 ? 1 : 0) << 10)) << 13);
+      S0.prv()[M + v] = M + v;
     }
   }
   __syncthreads();
 
   // ---- prologue 3: initial schedule (caller's CSR, or Algorithm 1 on the device)
   if (status == ASCHED_OK) {
-    const State S0 = sm.st(0);
     if (P.init_off) {
       int csr_bad = 0;
       for (int v = tid; v < V; v += nthr) {
@@ -564,7 +565,7 @@ __global__ void __launch_bounds__(1024, 1) tabu_kernel(const __grid_constant__ K
           continue;
         }
         int prev = M + v;
-        const int vp = v | ((sm.vtype[v] != 0 ? 1 : 0) << 16);
+        const int vw = nv_vw(S0.nv(M + v));
         for (int k = o0; k < o1; ++k) {
           const int m = P.init_route[k];
           if (m < 0 || m >= M) {
@@ -572,13 +573,13 @@ __global__ void __launch_bounds__(1024, 1) tabu_kernel(const __grid_constant__ K
             break;
           }
           atomicAdd(&sm.cnt[m], 1);
-          S0[ST_NXT][prev] = m;
-          S0[ST_PRV][m] = prev;
-          S0[ST_VEHP][m] = vp;
+          S0.nv(prev) = (S0.nv(prev) & ~kNodeMask) | m;
+          S0.prv()[m] = prev;
+          S0.nv(m) = (vw | ((P.heli_only ? P.heli_only[m] : 0) << 11)) << 13;
           prev = m;
         }
-        S0[ST_NXT][prev] = M + v;
-        S0[ST_PRV][M + v] = prev;
+        S0.nv(prev) = (S0.nv(prev) & ~kNodeMask) | (M + v);
+        S0.prv()[M + v] = prev;
       }
       csr_bad = __syncthreads_or(csr_bad);
       if (!csr_bad) {
@@ -590,10 +591,10 @@ __global__ void __launch_bounds__(1024, 1) tabu_kernel(const __grid_constant__ K
     } else {
       // Mission order: heli-only first, then by deadline, then by id.
       for (int m = tid; m < M; m += nthr) {
-        const int hm = sm.heli[m] ? 0 : 1, wmv = DL ? sm.wm[m] : 0;
+        const int hm = (P.heli_only && P.heli_only[m]) ? 0 : 1, wmv = DL ? sm.wm[m] : 0;
         int r = 0;
         for (int k = 0; k < M; ++k) {
-          const int hk = sm.heli[k] ? 0 : 1, wk = DL ? sm.wm[k] : 0;
+          const int hk = (P.heli_only && P.heli_only[k]) ? 0 : 1, wk = DL ? sm.wm[k] : 0;
           r += (hk < hm) || (hk == hm && (wk < wmv || (wk == wmv && k < m)));
         }
         sm.order[r] = m;
@@ -611,18 +612,18 @@ __global__ void __launch_bounds__(1024, 1) tabu_kernel(const __grid_constant__ K
         for (int k = 0; k < M && !fail; ++k) {
           const int m = sm.order[k];
           const int w = sm.wm[m];
+          const int heli = P.heli_only ? P.heli_only[m] : 0;
           uint64_t best = kNoKey;
           for (int v = lane; v < V; v += 32) {
-            const int ty = sm.vtype[v];
-            const int lb = ty * L;
+            const int tyl = sm.tyl[v];
             const int bl = sm.eloc[M + v];
-            const int a = sm.A[(lb + sm.gend[v]) * Mp + m];
-            const int bret = sm.B[(lb + bl) * Mp + m];
+            const int a = sm.A[(tyl + sm.gend[v]) * Mp + m];
+            const int bret = sm.B[(tyl + bl) * Mp + m];
             const int last = sm.glast[v];
-            const int old = last == M + v ? 0 : sm.B[(lb + bl) * Mp + last];
+            const int old = last == M + v ? 0 : sm.B[(tyl + bl) * Mp + last];
             const int app = a + bret - old;
             const int f = sm.gfl[v];
-            bool ok = !(sm.heli[m] && ty != 0);
+            bool ok = !(heli && sm.vtype[v] != 0);
             if (DL) ok = ok && (sm.gdep[v] + a <= w) && (w + bret <= c.horizon);
             int score;
             if (PEN) {
@@ -640,18 +641,16 @@ __global__ void __launch_bounds__(1024, 1) tabu_kernel(const __grid_constant__ K
           }
           if (lane == 0) {
             const int v = static_cast<int>(static_cast<uint32_t>(best));
-            const int ty = sm.vtype[v];
-            const int lb = ty * L;
+            const int tyl = sm.tyl[v];
             const int bl = sm.eloc[M + v];
             const int last = sm.glast[v];
-            const int a = sm.A[(lb + sm.gend[v]) * Mp + m];
-            const int bret = sm.B[(lb + bl) * Mp + m];
-            const int old = last == M + v ? 0 : sm.B[(lb + bl) * Mp + last];
-            S0[ST_NXT][last] = m;
-            S0[ST_PRV][m] = last;
-            S0[ST_NXT][m] = M + v;
-            S0[ST_PRV][M + v] = m;
-            S0[ST_VEHP][m] = S0[ST_VEHP][M + v];
+            const int a = sm.A[(tyl + sm.gend[v]) * Mp + m];
+            const int bret = sm.B[(tyl + bl) * Mp + m];
+            const int old = last == M + v ? 0 : sm.B[(tyl + bl) * Mp + last];
+            S0.nv(last) = (S0.nv(last) & ~kNodeMask) | m;
+            S0.prv()[m] = last;
+            S0.nv(m) = (M + v) | ((nv_vw(S0.nv(M + v)) | (heli << 11)) << 13);
+            S0.prv()[M + v] = m;
             sm.glast[v] = m;
             sm.gend[v] = sm.eloc[m];
             sm.gdep[v] = w;
@@ -669,57 +668,50 @@ __global__ void __launch_bounds__(1024, 1) tabu_kernel(const __grid_constant__ K
   // ---- prologue 4: flights, records, initial objective and feasibility
   int Z = 0;
   if (status == ASCHED_OK) {
-    const State S0 = sm.st(0);
-    for (int v = tid; v < V; v += nthr) S0[ST_FL][v] = 0;
+    const Arr fl0 = sm.gfl;  // flight sums (greedy scratch is free now)
+    __syncthreads();
+    for (int v = tid; v < V; v += nthr) fl0[v] = 0;
     __syncthreads();
     for (int t = tid; t < N; t += nthr) {
-      const int pv = S0[ST_PRV][t];
-      const int vv = S0[ST_VEHP][t] & 0xFFFF;
-      const int lb = sm.vtype[vv] * L;
+      const int pv = S0.prv()[t];
+      const int vw = nv_vw(S0.nv(t));
+      const int tyl = vw_plane(vw) * L;
       int contrib;
-      if (t < M) contrib = sm.A[(lb + sm.eloc[pv]) * Mp + t];
-      else contrib = pv == t ? 0 : sm.B[(lb + sm.sloc[t]) * Mp + pv];
-      atomicAdd(&S0[ST_FL][vv], contrib);
+      if (t < M) contrib = sm.A[(tyl + sm.eloc[pv]) * Mp + t];
+      else contrib = pv == t ? 0 : sm.B[(tyl + sm.sloc[t]) * Mp + pv];
+      atomicAdd(&fl0[vw_veh(vw)], contrib);
     }
     __syncthreads();
     int infeasible = 0;
     for (int t = tid; t < N; t += nthr) {
-      const int vp = S0[ST_VEHP][t];
-      const int vv = vp & 0xFFFF;
-      const int f = S0[ST_FL][vv];
-      write_records<PEN, DL>(sm, S0, c, t, S0[ST_NXT][t], S0[ST_PRV][t], vp, f);
-      const int pv = S0[ST_PRV][t];
+      const int nv = S0.nv(t), pv = S0.prv()[t];
+      const int vw = nv_vw(nv);
+      const int f = fl0[vw_veh(vw)];
+      const int tyl = vw_plane(vw) * L;
+      write_records<PEN, DL>(sm, S0, c, t, nv_next(nv), pv, vw, f);
       if (t < M) {
-        infeasible |= sm.heli[t] && (vp >> 16);
+        infeasible |= (vw >> 11) & (vw >> 10) & 1;
         if (DL) {
-          const int lb = sm.vtype[vv] * L;
           const int dep = pv < M ? sm.wm[pv] : 0;
-          infeasible |= dep + sm.A[(lb + sm.eloc[pv]) * Mp + t] > sm.wm[t];
+          infeasible |= dep + sm.A[(tyl + sm.eloc[pv]) * Mp + t] > sm.wm[t];
         }
       } else {
         if (!PEN) infeasible |= f > c.cap;
-        if (DL && pv != t) {
-          const int lb = sm.vtype[vv] * L;
-          infeasible |= sm.wm[pv] + sm.B[(lb + sm.sloc[t]) * Mp + pv] > c.horizon;
-        }
+        if (DL && pv != t) infeasible |= sm.wm[pv] + sm.B[(tyl + sm.sloc[t]) * Mp + pv] > c.horizon;
       }
     }
     if (__syncthreads_or(infeasible)) status = ASCHED_E_INFEASIBLE_INIT;
     if (warp == 0) {
       int z = 0;
       for (int v = lane; v < V; v += 32) {
-        const int f = S0[ST_FL][v];
+        const int f = fl0[v];
         z += f + (PEN ? c.lam * pos0(f - c.cap) : 0);
       }
       z = __reduce_add_sync(0xffffffffu, z);
       if (lane == 0) sm.misc[MISC_Z0] = z;
     }
-    for (int t = tid; t < N; t += nthr) sm.best[t] = S0[ST_NXT][t];
-    if (tid == 0 && C > 1) {
-      mbar_init(&sm.mbar[0], static_cast<uint32_t>(C));
-      mbar_init(&sm.mbar[1], static_cast<uint32_t>(C));
-      fence_mbar_init();
-    }
+    for (int t = tid; t < N; t += nthr) sm.best[t] = nv_next(S0.nv(t));
+    for (int i = tid; i < 2 * kMaxCluster; i += nthr) sm.slots()[i] = 0;
     __syncthreads();
     Z = sm.misc[MISC_Z0];
   }
@@ -729,171 +721,214 @@ __global__ void __launch_bounds__(1024, 1) tabu_kernel(const __grid_constant__ K
   const bool looped = status == ASCHED_OK;  // uniform over the cluster
   if (looped) {
     if (C > 1) cluster_sync_all();
+    // Static assignment over the item list [relocation pairs (N * ceil(M/2)) | swaps
+    // (M(M-1)/2)]: chunks of 32 consecutive items go round-robin to (CTA, warp), so
+    // every CTA gets an equal share and the lanes of a warp take consecutive items.
+    // A relocation item i is (y, h) = divmod(i, H) for missions 2h and 2h + 1; a swap
+    // item j is (row, a) = divmod(j, M) with b = (a + row + 1) mod M, which lists every
+    // pair a != b once. Coordinates advance by G without dividing.
     const int G = C * nthr;
-    const int g = rank * nthr + tid;
-    const int64_t Rn = static_cast<int64_t>(N) * M;
-    const int64_t Sn = static_cast<int64_t>(M) * (M - 1) / 2;
+    const int g = lane + 32 * (rank + C * warp);
+    const int H = (M + 1) / 2;
+    const int Rn = N * H;
+    const int Sn = M * (M - 1) / 2;
+    int r_y = N, r_h = 0, s_j = Sn, s_row = 0, s_a = 0, Gq = 0, Gr = 0, Sq = 0, Sr = 0;
+    if (M > 0) {
+      Gq = G / H;
+      Gr = G - Gq * H;
+      Sq = G / M;
+      Sr = G - Sq * M;
+      if (g < Rn) {
+        r_y = g / H;
+        r_h = g - r_y * H;
+      }
+      const int k = g < Rn ? (Rn - g + G - 1) / G : 0;  // relocation items of this thread
+      s_j = g + k * G - Rn;
+      if (s_j < Sn) {
+        s_row = s_j / M;
+        s_a = s_j - s_row * M;
+      }
+    }
     const int iters = DEBUG ? 1 : P.iterations;
     for (it = 0; it < iters; ++it) {
       const State S = sm.st(cur);
       const int it_eval = DEBUG ? P.dbg_it : it;
       const int zb_eval = DEBUG ? P.dbg_zbest : zbest;
       uint64_t key = kNoKey;
-      for (int64_t i = g; i < Rn; i += G) {
-        const int y = static_cast<int>(i / M);
-        const int m = static_cast<int>(i - static_cast<int64_t>(y) * M);
-        key = min_u64(key, eval_relocate<PEN, DL, DEBUG>(sm, S, c, y, m, it_eval, Z, zb_eval, P));
+      for (int y = r_y, h = r_h; y < N;) {
+        key = min_u64(key, eval_relocate_pair<PEN, DL, DEBUG>(sm, S, c, y, 2 * h, it_eval, Z, zb_eval, P));
+        h += Gr;
+        y += Gq;
+        if (h >= H) {
+          h -= H;
+          ++y;
+        }
       }
-      for (int64_t j = g; j < Sn; j += G) {
-        const int row = static_cast<int>(j / M);
-        const int a = static_cast<int>(j - static_cast<int64_t>(row) * M);
+      for (int j = s_j, row = s_row, a = s_a; j < Sn; j += G) {
         int b = a + row + 1;
         if (b >= M) b -= M;
         key = min_u64(key, eval_swap<PEN, DL, DEBUG>(sm, S, c, a, b, it_eval, Z, zb_eval, P));
+        a += Sr;
+        row += Sq;
+        if (a >= M) {
+          a -= M;
+          ++row;
+        }
       }
       key = warp_min_key(key);
-      if (lane == 0) sm.warpkey[warp] = key;
+      if (lane == 0) sm.warpkey()[warp] = key;
       __syncthreads();
-      uint64_t gk = warp_min_key(lane < nwarps ? sm.warpkey[lane] : kNoKey);
+      uint64_t gk = warp_min_key(lane < nwarps ? sm.warpkey()[lane] : kNoKey);
       bool timed_out = false;
       if (C > 1) {
+        // Push this CTA's key, tagged with the iteration, into slot [it & 1][rank] of
+        // every CTA; then every warp polls its own C slots until all carry this
+        // iteration's tag (bounded by the timeout).
         const int sb = it & 1;
+        const uint64_t tag = iter_tag(it);
         if (warp == 0 && lane < C) {
-          const uint32_t slot_addr = smem_u32(&sm.slots[sb * kMaxCluster + rank]);
-          const uint32_t bar_addr = smem_u32(&sm.mbar[sb]);
-          st_cluster_u64(mapa_rank(slot_addr, lane), gk);
-          mbar_arrive_cluster(mapa_rank(bar_addr, lane));
+          const uint32_t slot_addr = smem_u32(&sm.slots()[sb * kMaxCluster + rank]);
+          st_peer_u64(mapa_rank(slot_addr, lane), (gk & ~kTagMask) | tag);
         }
-        // The decision must be warp-uniform before the warp-wide reduction below.
-        const bool ok = __all_sync(0xffffffffu,
-                                   mbar_wait_bounded(&sm.mbar[sb], static_cast<uint32_t>((it >> 1) & 1),
-                                                     P.timeout_ns));
+        const uint32_t my_slot = smem_u32(&sm.slots()[sb * kMaxCluster + (lane < C ? lane : 0)]);
+        uint64_t v = ld_own_u64(my_slot);
+        bool ok = __all_sync(0xffffffffu, (v & kTagMask) == tag);
+        if (!ok) {
+          const uint64_t t0 = global_ns();
+          while (true) {
+            v = ld_own_u64(my_slot);
+            ok = __all_sync(0xffffffffu, (v & kTagMask) == tag);
+            if (ok) break;
+            // warp-uniform decision: lane 0's clock decides for the warp
+            const bool late = __shfl_sync(0xffffffffu, (int64_t)(global_ns() - t0) > P.timeout_ns, 0);
+            if (late) break;
+          }
+        }
         if (!ok) {
           timed_out = true;
         } else {
-          gk = warp_min_key(lane < C ? sm.slots[sb * kMaxCluster + lane] : kNoKey);
+          gk = warp_min_key(lane < C ? v : kNoKey) & ~kTagMask;
+          if ((gk >> 32) == 0xFFFFFFFFull) gk = kNoKey;  // real deltas never reach 2^31 - 1
         }
       }
       if (DEBUG) {
         if (rank == 0 && tid == 0 && !timed_out) *P.dbg_key = gk;
       } else if (!timed_out && gk != kNoKey) {
-        // ---- apply the chosen move: every thread decodes it, then rewrites its nodes
+        // ---- apply the chosen move: every thread decodes it from the current buffer,
+        // then rewrites the records of its nodes into the other buffer.
         const State S2 = sm.st(cur ^ 1);
-        const uint32_t id = static_cast<uint32_t>(gk);
-        const bool is_swap = (id & kSwapBit) != 0;
-        int m = 0, y = 0, e = 0, s = 0, x = 0, a = 0, b = 0, pa = 0, na = 0, pb = 0, nb = 0;
-        bool adjA = false, adjB = false;
-        int va, vb, vpa, vpb, fa2, fb2 = 0;
-        if (!is_swap) {
-          m = static_cast<int>(id >> kIdShift);
-          y = static_cast<int>(id & kIdMask);
-          e = S[ST_PRV][m];
-          s = S[ST_NXT][m];
-          x = S[ST_PRV][y];
-          vpa = S[ST_VEHP][m];
-          vpb = S[ST_VEHP][y];
-          va = vpa & 0xFFFF;
-          vb = vpb & 0xFFFF;
-          const int ins = sm.A[S[ST_ROWA][y] + m] + sm.B[S[ST_ROWB][y] + m] - S[ST_INLEG][y];
-          const int rem = S[ST_REM][m];
-          const int fa = S[ST_FL][va];
-          if (va == vb) {
-            fa2 = fa + rem + ins;
-          } else {
-            fa2 = fa + rem;
-            fb2 = S[ST_FL][vb] + ins;
-          }
-        } else {
-          a = static_cast<int>((id >> kIdShift) & kIdMask);
-          b = static_cast<int>(id & kIdMask);
-          vpa = S[ST_VEHP][a];
-          vpb = S[ST_VEHP][b];
-          va = vpa & 0xFFFF;
-          vb = vpb & 0xFFFF;
-          pa = S[ST_PRV][a];
-          na = S[ST_NXT][a];
-          pb = S[ST_PRV][b];
-          nb = S[ST_NXT][b];
-          adjA = na == b;
-          adjB = nb == a;
-          const int t1 = sm.A[(adjB ? S[ST_ROWE][a] : S[ST_ROWA][a]) + b];
-          const int t2 = sm.B[S[ST_ROWBN][a] + (adjA ? a : b)];
-          const int t3 = sm.A[(adjA ? S[ST_ROWE][b] : S[ST_ROWA][b]) + a];
-          const int t4 = sm.B[S[ST_ROWBN][b] + (adjB ? b : a)];
-          const int da = t1 + t2 - S[ST_SLOT][a];
-          const int db = t3 + t4 - S[ST_SLOT][b];
-          const int fa = S[ST_FL][va];
-          if (va == vb) {
-            fa2 = fa + da + db;
-          } else {
-            fa2 = fa + da;
-            fb2 = S[ST_FL][vb] + db;
-          }
-        }
         const int Znew = Z + key_delta(gk);
         const bool improved = Znew < zbest;
-        for (int t = tid; t < N; t += nthr) {
-          int nx = S[ST_NXT][t], pv = S[ST_PRV][t], vp = S[ST_VEHP][t];
+        if (warp * 32 < N) {  // only warps that own nodes need the decoded move
+          const uint32_t id = static_cast<uint32_t>(gk);
+          const bool is_swap = (id & kSwapBit) != 0;
+          int m = 0, y = 0, e = 0, s = 0, x = 0, a = 0, b = 0, pa = 0, na = 0, pb = 0, nb = 0;
+          bool adjA = false, adjB = false;
+          int vwa, vwb, fa2, fb2 = 0;
           if (!is_swap) {
-            if (t == e) nx = s;
-            if (t == s) pv = e;
-            if (t == x) nx = m;
-            if (t == y) pv = m;
-            if (t == m) {
-              nx = y;
-              pv = x;
-              vp = vpb;
-            }
-          } else if (adjA) {  // pa -> a -> b -> nb  becomes  pa -> b -> a -> nb
-            if (t == pa) nx = b;
-            if (t == nb) pv = a;
-            if (t == b) {
-              pv = pa;
-              nx = a;
-            }
-            if (t == a) {
-              pv = b;
-              nx = nb;
-            }
-          } else if (adjB) {  // pb -> b -> a -> na  becomes  pb -> a -> b -> na
-            if (t == pb) nx = a;
-            if (t == na) pv = b;
-            if (t == a) {
-              pv = pb;
-              nx = b;
-            }
-            if (t == b) {
-              pv = a;
-              nx = na;
+            m = static_cast<int>(id >> kIdShift);
+            y = static_cast<int>(id & kIdMask);
+            const int2 r = S.r2()[m];
+            const int4 g = S.y4()[y];
+            vwa = nv_vw(r.x);
+            vwb = nv_vw(g.w);
+            s = nv_next(r.x);
+            e = S.prv()[m];
+            x = S.prv()[y];
+            const int ins = sm.A[g.x + m] + sm.B[g.y + m] - g.z;
+            const int fa = S.fb()[vw_veh(vwa)] + c.cap;
+            if (vw_veh(vwa) == vw_veh(vwb)) {
+              fa2 = fa + r.y + ins;
+            } else {
+              fa2 = fa + r.y;
+              fb2 = S.fb()[vw_veh(vwb)] + c.cap + ins;
             }
           } else {
-            if (t == pa) nx = b;
-            if (t == na) pv = b;
-            if (t == pb) nx = a;
-            if (t == nb) pv = a;
-            if (t == a) {
-              pv = pb;
-              nx = nb;
-              vp = vpb;
-            }
-            if (t == b) {
-              pv = pa;
-              nx = na;
-              vp = vpa;
+            a = static_cast<int>((id >> kIdShift) & kIdMask);
+            b = static_cast<int>(id & kIdMask);
+            const SwapParts q = swap_parts(sm, S, c, a, b);
+            vwa = nv_vw(q.sa.x);
+            vwb = nv_vw(q.sb.x);
+            na = nv_next(q.sa.x);
+            nb = nv_next(q.sb.x);
+            pa = S.prv()[a];
+            pb = S.prv()[b];
+            adjA = q.adjA;
+            adjB = q.adjB;
+            const int da = q.t1 + q.t2 - q.sa.w;
+            const int db = q.t3 + q.t4 - q.sb.w;
+            const int fa = S.fb()[vw_veh(vwa)] + c.cap;
+            if (vw_veh(vwa) == vw_veh(vwb)) {
+              fa2 = fa + da + db;
+            } else {
+              fa2 = fa + da;
+              fb2 = S.fb()[vw_veh(vwb)] + c.cap + db;
             }
           }
-          const int vv = vp & 0xFFFF;
-          const int f2 = vv == va ? fa2 : (vv == vb ? fb2 : S[ST_FL][vv]);
-          write_records<PEN, DL>(sm, S2, c, t, nx, pv, vp, f2);
-          if (t >= M) S2[ST_FL][t - M] = f2;
-          if (improved) sm.best[t] = nx;
-        }
-        if (tid == 0) {
-          if (!is_swap) {
-            sm.tabu[va * Mp + m] = it + P.tenure;
-          } else {
-            sm.tabu[va * Mp + a] = it + P.tenure;
-            sm.tabu[vb * Mp + b] = it + P.tenure;
+          const int va = vw_veh(vwa), vb = vw_veh(vwb);
+          for (int t = tid; t < N; t += nthr) {
+            const int nv = S.nv(t);
+            int nx = nv_next(nv), pv = S.prv()[t], vw = nv_vw(nv);
+            if (!is_swap) {
+              if (t == e) nx = s;
+              if (t == s) pv = e;
+              if (t == x) nx = m;
+              if (t == y) pv = m;
+              if (t == m) {
+                nx = y;
+                pv = x;
+                vw = vw_move(vwb, vw);
+              }
+            } else if (adjA) {  // pa -> a -> b -> nb  becomes  pa -> b -> a -> nb
+              if (t == pa) nx = b;
+              if (t == nb) pv = a;
+              if (t == b) {
+                pv = pa;
+                nx = a;
+              }
+              if (t == a) {
+                pv = b;
+                nx = nb;
+              }
+            } else if (adjB) {  // pb -> b -> a -> na  becomes  pb -> a -> b -> na
+              if (t == pb) nx = a;
+              if (t == na) pv = b;
+              if (t == a) {
+                pv = pb;
+                nx = b;
+              }
+              if (t == b) {
+                pv = a;
+                nx = na;
+              }
+            } else {
+              if (t == pa) nx = b;
+              if (t == na) pv = b;
+              if (t == pb) nx = a;
+              if (t == nb) pv = a;
+              if (t == a) {
+                pv = pb;
+                nx = nb;
+                vw = vw_move(vwb, vwa);
+              }
+              if (t == b) {
+                pv = pa;
+                nx = na;
+                vw = vw_move(vwa, vwb);
+              }
+            }
+            const int vv = vw_veh(vw);
+            const int f2 = vv == va ? fa2 : (vv == vb ? fb2 : S.fb()[vv] + c.cap);
+            write_records<PEN, DL>(sm, S2, c, t, nx, pv, vw, f2);
+            if (improved) sm.best[t] = nx;
+          }
+          if (tid == 0) {
+            if (!is_swap) {
+              sm.tabu[va * Mp + m] = it + P.tenure;
+            } else {
+              sm.tabu[va * Mp + a] = it + P.tenure;
+              sm.tabu[vb * Mp + b] = it + P.tenure;
+            }
           }
         }
         Z = Znew;
@@ -916,7 +951,7 @@ __global__ void __launch_bounds__(1024, 1) tabu_kernel(const __grid_constant__ K
 
   // ---- epilogue: best schedule in CSR form (rank 0 writes every output)
   if (rank == 0 && !DEBUG && status == ASCHED_OK && P.out_off) {
-    int* lens = sm.order;  // scratch reuse
+    const Arr lens = sm.gfl;  // scratch reuse (V entries)
     int walk_bad = 0;
     for (int v = tid; v < V; v += nthr) {
       int n = 0, t = sm.best[M + v];
@@ -946,8 +981,7 @@ __global__ void __launch_bounds__(1024, 1) tabu_kernel(const __grid_constant__ K
     if (sm.misc[MISC_CSR_BAD]) walk_bad = 1;
     if (!walk_bad) {
       for (int v = tid; v < V; v += nthr) {
-        const int ty = sm.vtype[v];
-        const int32_t* T = P.travel + static_cast<int64_t>(ty) * L * L;
+        const int32_t* T = P.travel + static_cast<int64_t>(sm.vtype[v]) * L * L;
         const int bl = sm.eloc[M + v];
         int o = 0;
         for (int w = 0; w < v; ++w) o += lens[w];
@@ -970,7 +1004,7 @@ __global__ void __launch_bounds__(1024, 1) tabu_kernel(const __grid_constant__ K
     P.info[ASCHED_INFO_STATUS] = status;
     P.info[ASCHED_INFO_Z_BEST] = zbest;
     P.info[ASCHED_INFO_BEST_IT] = best_it;
-    P.info[ASCHED_INFO_Z_INIT] = status == ASCHED_OK || status == ASCHED_E_TIMEOUT ? sm.misc[MISC_Z0] : 0;
+    P.info[ASCHED_INFO_Z_INIT] = sm.misc[MISC_Z0];
     P.info[ASCHED_INFO_Z_FINAL] = Z;
     P.info[ASCHED_INFO_ITERS] = it;
     P.info[6] = 0;
@@ -1009,7 +1043,7 @@ int check_sizes(const asched_instance* inst, const asched_params* p) {
   if (p->cluster_size != 0 && p->cluster_size != 1 && p->cluster_size != 2 && p->cluster_size != 4 &&
       p->cluster_size != 8 && p->cluster_size != 16)
     return ASCHED_E_INVALID;
-  if (p->block_threads != 0 && (p->block_threads < 64 || p->block_threads > 1024 || p->block_threads % 32))
+  if (p->block_threads != 0 && (p->block_threads < 64 || p->block_threads > kMaxThreads || p->block_threads % 32))
     return ASCHED_E_INVALID;
   if (p->timeout_ns < 0 || p->flags != 0) return ASCHED_E_INVALID;
   return ASCHED_OK;
@@ -1038,7 +1072,7 @@ int make_plan(const asched_instance* inst, const asched_params* p, asched_plan_t
   int threads = p->block_threads;
   if (threads == 0) {
     const int64_t want = items > M + V ? items : M + V;
-    threads = want >= 1024 ? 1024 : (want <= 64 ? 64 : round_up(static_cast<int>(want), 32));
+    threads = want >= kMaxThreads ? kMaxThreads : (want <= 64 ? 64 : round_up(static_cast<int>(want), 32));
   }
   int cl = p->cluster_size;
   if (cl == 0) {

@@ -82,7 +82,7 @@ def test_check_instance_host_rejects_bad_params():
     assert api.check_instance_host(inst, _params(tenure=-1)) == api.E_INVALID
     assert api.check_instance_host(inst, _params(cluster_size=5)) == api.E_INVALID
     assert api.check_instance_host(inst, _params(block_threads=100)) == api.E_INVALID
-    assert api.check_instance_host(inst, _params(block_threads=2048)) == api.E_INVALID
+    assert api.check_instance_host(inst, _params(block_threads=1024)) == api.E_INVALID
     assert api.check_instance_host(inst, _params(cluster_size=16, block_threads=64)) == api.OK
 
 

@@ -88,8 +88,8 @@ def test_eval_neighbourhood_matches_oracle(name, mk, mode, tenure):
     assert checked > 0
 
 
-@pytest.mark.parametrize("cluster,threads", [(1, 64), (1, 1024), (2, 96), (4, 256), (8, 512),
-                                             (16, 1024), (16, 64)])
+@pytest.mark.parametrize("cluster,threads", [(1, 64), (1, 512), (2, 96), (4, 256), (8, 512),
+                                             (16, 512), (16, 64)])
 def test_eval_independent_of_launch_shape(cluster, threads):
     inst = gen.random_instance(31, n_loc=12, n_vehicles=7, n_missions=45, n_types=2,
                                heli_only_frac=0.2, duty_cap=1200, max_minutes=140)
@@ -152,7 +152,7 @@ def test_solve_trajectory_matches_oracle(name, mk, mode, tenure, iters):
     _check_solve_vs_oracle(mk(), mode, tenure, iters)
 
 
-@pytest.mark.parametrize("cluster,threads", [(1, 1024), (2, 512), (4, 128), (8, 1024), (16, 256)])
+@pytest.mark.parametrize("cluster,threads", [(1, 512), (2, 512), (4, 128), (8, 448), (16, 256)])
 def test_trajectory_independent_of_launch_shape(cluster, threads):
     inst = gen.random_instance(51, n_loc=14, n_vehicles=8, n_missions=40, n_types=2,
                                heli_only_frac=0.2, duty_cap=900, max_minutes=120)
