@@ -16,6 +16,7 @@ cores instead (bounded iteration samples of the same instance).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -39,6 +40,11 @@ WORKLOAD = ("paper-shaped single instance: 12 bases, 20 vehicles, 60 facilities 
 # design notes): a relocation is 23 ops, a swap 34, mixed in proportion.
 OPS_RELOCATE = 23
 OPS_SWAP = 34
+# DRAM bytes (read + write) of one solve launch, from the ncu capture summarised in
+# profiles/tabu_kernel_paper_shaped.md. Valid only for the kernel source it was taken
+# on; any other source reports traffic as null.
+TRAFFIC_BYTES = 114432
+TRAFFIC_SOURCE_SHA = "eeb3fc4acd3cc869"
 
 
 def _env_int(k, d):
@@ -46,6 +52,13 @@ def _env_int(k, d):
         return int(os.environ.get(k, d))
     except ValueError:
         return d
+
+
+def traffic_bytes():
+    src = os.path.join(ROOT, "paper_2002_11710_gb300", "csrc", "asched.cu")
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    return TRAFFIC_BYTES if sha == TRAFFIC_SOURCE_SHA else None
 
 
 def moves_split(M, V):
@@ -114,6 +127,23 @@ def cpu_oracle_sample(inst, p, iterations):
     M, V = inst.n_missions, inst.n_vehicles
     n = (M * (M + V - 2) + M * (M - 1) // 2) * iterations
     return n / dt, dt
+
+
+def max_over_ranks(seconds, world, device):
+    """The slowest rank's time (all ranks call this; world 1 returns the input)."""
+    if world <= 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / seconds
 
 
 def run_reference(args, rank, world):
@@ -197,10 +227,7 @@ def run_gpu(args, rank, world, local_rank):
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     dev_s = sum(step_ms) / 1000.0
     clk = clocks.stop() if clocks else None
-    if world > 1:
-        t = torch.tensor([dev_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_s = float(t.item())
+    dev_s = max_over_ranks(dev_s, world, dev)
     # end to end through the public API from host data
     pinned = api.pin_instance(inst)
     e2e_times = []
@@ -218,14 +245,11 @@ def run_gpu(args, rank, world, local_rank):
         d2h = sum(int(v.nbytes) for v in res.values())
         assert int(res["info"][api.INFO_Z_BEST]) == z_best
     e2e_s = sum(e2e_times)
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, world, dev)
     if rank != 0:
         return
-    value = moves_step * args.steps * world / dev_s
-    e2e_value = moves_step * args.steps * world / e2e_s
+    value = whole_job_rate(moves_step * args.steps, world, dev_s)
+    e2e_value = whole_job_rate(moves_step * args.steps, world, e2e_s)
     launch_s = statistics.mean(step_ms) / 1000.0
     ops = (R * OPS_RELOCATE + S * OPS_SWAP) * p.iterations
     peaks = {}
@@ -258,7 +282,7 @@ def run_gpu(args, rank, world, local_rank):
         "gpu_launches": args.steps,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
-                     "frac": achieved / peak_tops, "traffic": None,
+                     "frac": achieved / peak_tops, "traffic": traffic_bytes(),
                      "peak_basis": f"{sm_count} SMs x {int_lanes} int32 lanes/clk x {sm_max_mhz:.0f} MHz",
                      "frac_of_sms_used": achieved / (peak_tops * plan.cluster_size / sm_count)},
         "cpu_baseline": None if cpu_rate is None else {
