@@ -246,6 +246,7 @@ def run_gpu(args, rank, world, local_rank):
         assert int(res["info"][api.INFO_Z_BEST]) == z_best
     e2e_s = sum(e2e_times)
     e2e_s = max_over_ranks(e2e_s, world, dev)
+    batched = run_batched(args, dev) if args.batched else None
     if rank != 0:
         return
     value = whole_job_rate(moves_step * args.steps, world, dev_s)
@@ -285,12 +286,61 @@ def run_gpu(args, rank, world, local_rank):
                      "frac": achieved / peak_tops, "traffic": traffic_bytes(),
                      "peak_basis": f"{sm_count} SMs x {int_lanes} int32 lanes/clk x {sm_max_mhz:.0f} MHz",
                      "frac_of_sms_used": achieved / (peak_tops * plan.cluster_size / sm_count)},
+        "batched": batched,
         "cpu_baseline": None if cpu_rate is None else {
             "value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {args.cpu_iterations} of 5,000 iterations, same instance, {cpu_dt:.1f} s"},
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
+
+
+def run_batched(args, dev):
+    """The batched workload: 1,024 instances (V ~ U[3, 30], M ~ U[10, 200], paper-shaped
+    geography, 2,000 iterations each) in one persistent launch, block size picked by the
+    autotuner, against the same instances as 1,024 single-instance launches."""
+    import torch
+
+    from paper_2002_11710_gb300 import api, gen
+
+    insts = [gen.batched_member(i) for i in range(1024)]
+    p = gen.BATCHED_PARAMS
+    moves = sum(api.num_moves(i.n_missions, i.n_vehicles) for i in insts) * p.iterations
+    bp = api.BatchProblem(insts, dev)
+    thr, tune = api.autotune_batch(bp, api.params_from(p))
+    params = api.params_from(p, block_threads=thr)
+    out = bp.alloc_output()
+    for _ in range(max(1, args.warmup // 2)):
+        api.solve_batch(bp, params, out=out)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(3):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        api.solve_batch(bp, params, out=out)
+        b.record()
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    ok = int((out.info.view(-1, api.INFO_LEN)[:, api.INFO_STATUS] == 0).sum())
+    single = api.params_from(p)
+    dps = [api.DeviceProblem(i, dev) for i in insts]
+    outs = [api.alloc_output(d, p.iterations) for d in dps]
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for d, o in zip(dps, outs):
+        api.solve(d, single, out=o)
+    b.record()
+    b.synchronize()
+    seq_ms = a.elapsed_time(b)
+    t = statistics.median(ms)
+    return {"workload": "1,024 instances, V ~ U[3,30], M ~ U[10,200], 2,000 iterations each",
+            "ms": t, "solves_per_s": 1024 / t * 1e3, "moves_per_s": moves / t * 1e3,
+            "block_threads": thr, "autotune_ms": tune, "instances_ok": ok,
+            "sequential_ms": seq_ms, "sequential_solves_per_s": 1024 / seq_ms * 1e3,
+            "speedup_vs_sequential": seq_ms / t, "gpu_launches": 2}
 
 
 def main():
@@ -304,6 +354,8 @@ def main():
     ap.add_argument("--cpu-iterations", type=int, default=600)
     ap.add_argument("--ref-iterations", type=int, default=100)
     ap.add_argument("--int32-lanes-per-sm", type=int, default=128)
+    ap.add_argument("--no-batched", dest="batched", action="store_false",
+                    help="skip the 1,024-instance batched measurement")
     args = ap.parse_args()
     world = _env_int("WORLD_SIZE", 1)
     rank = _env_int("RANK", 0)

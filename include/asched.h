@@ -209,6 +209,66 @@ int asched_eval_neighbourhood(const asched_instance* inst, const asched_params* 
                               int32_t* delta_out, uint8_t* flags_out, uint32_t* id_out,
                               unsigned long long* best_key_out, int32_t* info, void* stream);
 
+/* ---------------------------------------------------------------- batches ----------
+ * Many independent instances solved by one persistent launch (one CTA per instance
+ * at a time, instances taken largest first from a device work queue). The arrays of
+ * all instances are concatenated; instance b owns
+ *   locations  [loc_off[b], loc_off[b+1]),  L_b = loc_off[b+1] - loc_off[b]
+ *   vehicles   [veh_off[b], veh_off[b+1]),  V_b >= 1
+ *   missions   [mis_off[b], mis_off[b+1]),  M_b >= 0
+ *   travel     n_types * L_b * L_b minutes starting at travel_off[b]
+ * Location indices (veh_base, pickup, delivery) are local to the instance. The three
+ * offset arrays are given twice: h_* in host memory (read by the call to size the
+ * launch) and as device copies (read by the kernel); they must agree.
+ * Every instance shares the asched_params (cluster_size must be 0 or 1). */
+typedef struct {
+  int32_t n_instances;
+  int32_t n_types;
+  const int32_t* h_loc_off;  /* HOST [n_instances + 1] */
+  const int32_t* h_veh_off;  /* HOST [n_instances + 1] */
+  const int32_t* h_mis_off;  /* HOST [n_instances + 1] */
+  const int32_t* loc_off;    /* device [n_instances + 1] */
+  const int32_t* veh_off;    /* device [n_instances + 1] */
+  const int32_t* mis_off;    /* device [n_instances + 1] */
+  const int64_t* travel_off; /* device [n_instances] */
+  const int32_t* travel;     /* device, concatenated */
+  const int32_t* veh_base;   /* device [veh_off[B]] */
+  const int32_t* veh_type;   /* device [veh_off[B]] or NULL */
+  const int32_t* pickup;     /* device [mis_off[B]] */
+  const int32_t* delivery;   /* device [mis_off[B]] */
+  const int32_t* heli_only;  /* device [mis_off[B]] or NULL */
+  const int32_t* deadline;   /* device [mis_off[B]] or NULL (then no instance has deadlines) */
+  const int32_t* duty_cap;   /* device [n_instances] */
+  const int32_t* horizon;    /* device [n_instances] */
+} asched_batch;
+
+/* Outputs of asched_solve_batch (device memory), per instance b:
+ *   route_off  V_b + 1 entries at route_off[veh_off[b] + b], offsets local to b
+ *   route      M_b entries at route[mis_off[b]]
+ *   flight, overflow  V_b entries at [veh_off[b]] (may be NULL)
+ *   info       ASCHED_INFO_LEN entries at info[b * ASCHED_INFO_LEN] */
+typedef struct {
+  int32_t* route_off;
+  int32_t* route;
+  int32_t* flight;
+  int32_t* overflow;
+  int32_t* info;
+} asched_batch_result;
+
+/* Device workspace asched_solve_batch needs for n_instances (a queue counter and the
+ * processing order): 4 * (n_instances + 1) bytes. Host only. */
+int asched_batch_workspace_bytes(int32_t n_instances, size_t* out);
+
+/* Tabu search (Algorithm 3, greedy start of Algorithm 1) on every instance of the
+ * batch: one small ordering kernel, then one persistent launch on `stream`. Each
+ * instance's result equals what asched_solve returns for it alone. workspace is
+ * caller-owned device memory of at least asched_batch_workspace_bytes; it is
+ * overwritten, and two batches in flight at once need two workspaces. Returns
+ * ASCHED_E_TOO_LARGE if some instance does not fit the on-chip layout. */
+int asched_solve_batch(const asched_batch* batch, const asched_params* params,
+                       const asched_batch_result* out, void* workspace, size_t workspace_bytes,
+                       void* stream);
+
 #ifdef __cplusplus
 }
 #endif

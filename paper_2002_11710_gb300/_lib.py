@@ -57,6 +57,18 @@ class Result(ctypes.Structure):
                 ("traj_move", P), ("traj_z", P)]
 
 
+class Batch(ctypes.Structure):
+    _fields_ = [("n_instances", ctypes.c_int32), ("n_types", ctypes.c_int32),
+                ("h_loc_off", P), ("h_veh_off", P), ("h_mis_off", P),
+                ("loc_off", P), ("veh_off", P), ("mis_off", P), ("travel_off", P),
+                ("travel", P), ("veh_base", P), ("veh_type", P), ("pickup", P), ("delivery", P),
+                ("heli_only", P), ("deadline", P), ("duty_cap", P), ("horizon", P)]
+
+
+class BatchResult(ctypes.Structure):
+    _fields_ = [("route_off", P), ("route", P), ("flight", P), ("overflow", P), ("info", P)]
+
+
 # Every entry point of include/asched.h with its ctypes signature.
 SIGNATURES = {
     "asched_abi_version": (ctypes.c_int, []),
@@ -67,6 +79,8 @@ SIGNATURES = {
     "asched_solve": (ctypes.c_int, [P, P, P, P, P, P]),
     "asched_eval_neighbourhood": (ctypes.c_int, [P, P, P, P, P, ctypes.c_int32, ctypes.c_int32,
                                                  P, P, P, P, P, P]),
+    "asched_batch_workspace_bytes": (ctypes.c_int, [ctypes.c_int32, P]),
+    "asched_solve_batch": (ctypes.c_int, [P, P, P, P, ctypes.c_size_t, P]),
 }
 
 _lock = threading.Lock()

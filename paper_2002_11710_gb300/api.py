@@ -235,3 +235,139 @@ def solve_host(inst, params: _lib.Params, trajectory: bool = False, device="cuda
         res["traj_move"] = res["traj_move"][: params.iterations].view(np.uint32)
         res["traj_z"] = res["traj_z"][: params.iterations]
     return res
+
+
+# ------------------------------------------------------------------------- batches --
+
+class BatchProblem:
+    """Many instances packed into concatenated device arrays (the asched_batch layout).
+
+    All instances must have the same number of travel layers, and either all or none
+    have deadlines (heli-only flags may be missing on some: they count as 0)."""
+
+    def __init__(self, instances, device="cuda"):
+        self.device = torch.device(device)
+        insts = list(instances)
+        self.B = len(insts)
+        nt = {int(i.travel.shape[0]) for i in insts}
+        if len(nt) > 1:
+            raise ValueError("every instance needs the same number of travel layers")
+        self.n_types = nt.pop() if insts else 1
+        dl = {i.deadline is not None for i in insts}
+        if len(dl) > 1:
+            raise ValueError("either every instance has deadlines or none has")
+        self.has_deadlines = bool(dl and dl.pop())
+        L = np.array([i.travel.shape[1] for i in insts], np.int64)
+        V = np.array([len(i.veh_base) for i in insts], np.int64)
+        M = np.array([len(i.pickup) for i in insts], np.int64)
+        self.h_loc_off = np.concatenate([[0], np.cumsum(L)]).astype(np.int32)
+        self.h_veh_off = np.concatenate([[0], np.cumsum(V)]).astype(np.int32)
+        self.h_mis_off = np.concatenate([[0], np.cumsum(M)]).astype(np.int32)
+        tsz = self.n_types * L * L
+        self.h_travel_off = np.concatenate([[0], np.cumsum(tsz)])[:-1].astype(np.int64)
+
+        def cat(arrs, dtype=np.int32):
+            arrs = [np.ascontiguousarray(a, dtype=dtype).reshape(-1) for a in arrs]
+            out = np.concatenate(arrs) if arrs else np.zeros(0, dtype)
+            return out if out.size else np.zeros(1, dtype)
+
+        dev = self.device
+        t = lambda a, dt=torch.int32: torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)  # noqa: E731
+        self.loc_off = t(self.h_loc_off)
+        self.veh_off = t(self.h_veh_off)
+        self.mis_off = t(self.h_mis_off)
+        self.travel_off = t(self.h_travel_off if self.B else np.zeros(1, np.int64), torch.int64)
+        self.travel = t(cat([i.travel for i in insts]))
+        self.veh_base = t(cat([i.veh_base for i in insts]))
+        self.veh_type = t(cat([i.veh_type for i in insts]))
+        self.pickup = t(cat([i.pickup for i in insts]))
+        self.delivery = t(cat([i.delivery for i in insts]))
+        any_heli = any(i.heli_only is not None for i in insts)
+        self.heli_only = t(cat([i.heli_only if i.heli_only is not None else np.zeros(len(i.pickup))
+                                for i in insts])) if any_heli else None
+        self.deadline = t(cat([i.deadline for i in insts])) if self.has_deadlines else None
+        self.duty_cap = t(np.array([i.duty_cap for i in insts] or [0], np.int32))
+        self.horizon = t(np.array([i.horizon for i in insts] or [0], np.int32))
+        ws = ctypes.c_size_t(0)
+        _lib.check(_lib.load().asched_batch_workspace_bytes(self.B, ctypes.byref(ws)),
+                   "asched_batch_workspace_bytes")
+        self.workspace = torch.zeros((ws.value + 3) // 4, dtype=torch.int32, device=dev)
+        hp = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+        self.struct = _lib.Batch(self.B, self.n_types, hp(self.h_loc_off), hp(self.h_veh_off),
+                                 hp(self.h_mis_off), _ptr(self.loc_off), _ptr(self.veh_off),
+                                 _ptr(self.mis_off), _ptr(self.travel_off), _ptr(self.travel),
+                                 _ptr(self.veh_base), _ptr(self.veh_type), _ptr(self.pickup),
+                                 _ptr(self.delivery), _ptr(self.heli_only), _ptr(self.deadline),
+                                 _ptr(self.duty_cap), _ptr(self.horizon))
+
+    def alloc_output(self):
+        dev = self.device
+        nv = int(self.h_veh_off[-1])
+        nm = int(self.h_mis_off[-1])
+        z = lambda n: torch.zeros(max(n, 1), dtype=torch.int32, device=dev)  # noqa: E731
+        return BatchOutput(route_off=z(nv + self.B), route=z(nm), flight=z(nv), overflow=z(nv),
+                           info=z(self.B * INFO_LEN))
+
+    def unpack(self, out: "BatchOutput", b: int):
+        """Instance b's results as numpy arrays (call after synchronising)."""
+        vo, v1 = int(self.h_veh_off[b]), int(self.h_veh_off[b + 1])
+        mo, m1 = int(self.h_mis_off[b]), int(self.h_mis_off[b + 1])
+        return {"route_off": out.route_off[vo + b: v1 + b + 1].cpu().numpy(),
+                "route": out.route[mo:m1].cpu().numpy(),
+                "flight": out.flight[vo:v1].cpu().numpy(),
+                "overflow": out.overflow[vo:v1].cpu().numpy(),
+                "info": out.info[b * INFO_LEN:(b + 1) * INFO_LEN].cpu().numpy()}
+
+
+@dataclasses.dataclass
+class BatchOutput:
+    route_off: torch.Tensor
+    route: torch.Tensor
+    flight: torch.Tensor
+    overflow: torch.Tensor
+    info: torch.Tensor
+
+    def struct(self):
+        return _lib.BatchResult(_ptr(self.route_off), _ptr(self.route), _ptr(self.flight),
+                                _ptr(self.overflow), _ptr(self.info))
+
+
+def solve_batch(bp: BatchProblem, params: _lib.Params, out: Optional[BatchOutput] = None,
+                stream: Optional[torch.cuda.Stream] = None) -> BatchOutput:
+    """Queue asched_solve_batch on `stream` (default: torch's current stream)."""
+    if out is None:
+        out = bp.alloc_output()
+    s = stream if stream is not None else torch.cuda.current_stream(bp.device)
+    res = out.struct()
+    rc = _lib.load().asched_solve_batch(ctypes.byref(bp.struct), ctypes.byref(params),
+                                        ctypes.byref(res), _ptr(bp.workspace),
+                                        ctypes.c_size_t(bp.workspace.numel() * 4),
+                                        ctypes.c_void_p(s.cuda_stream))
+    _lib.check(rc, "asched_solve_batch")
+    return out
+
+
+def autotune_batch(bp: BatchProblem, params: _lib.Params, candidates=(512, 384, 256, 128),
+                   probe_iterations: int = 200, repeats: int = 2):
+    """Pick the block size for a batch by timing short probe runs of each candidate
+    (CUDA events on the current stream). Results never depend on the choice; only the
+    time does. Returns (best block size, {candidate: ms})."""
+    probe = _lib.Params(params.tenure, min(params.iterations, probe_iterations), params.cap_mode,
+                        params.lam, params.cluster_size, 0, params.timeout_ns, params.flags)
+    out = bp.alloc_output()
+    times = {}
+    for thr in candidates:
+        probe.block_threads = int(thr)
+        solve_batch(bp, probe, out=out)  # warm-up
+        best = None
+        for _ in range(repeats):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            solve_batch(bp, probe, out=out)
+            b.record()
+            b.synchronize()
+            ms = a.elapsed_time(b)
+            best = ms if best is None else min(best, ms)
+        times[int(thr)] = best
+    return min(times, key=times.get), times

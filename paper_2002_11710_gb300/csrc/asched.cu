@@ -456,19 +456,19 @@ __device__ __forceinline__ uint64_t eval_swap(const Smem& sm, const State& S, co
 
 // ------------------------------------------------------------------ the kernel -----
 
+// One complete search (prologue, every iteration, epilogue) of the instance in P by
+// the C CTAs of this cluster (this CTA is `rank`), with shared memory laid out by lay.
 template <bool PEN, bool DL, bool DEBUG>
-__global__ void __launch_bounds__(kMaxThreads, 1) tabu_kernel(const __grid_constant__ KParams P) {
-  const Smem sm = carve(P.lay);
+__device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, const int C, const int rank) {
+  const Smem sm = carve(lay);
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
-  const int C = P.cluster;
-  const int rank = C > 1 ? static_cast<int>(cluster_rank()) : 0;
   Ctx c;
   c.M = P.M;
   c.V = P.V;
   c.N = P.M + P.V;
   c.L = P.L;
-  c.Mp = P.lay.Mp;
+  c.Mp = lay.Mp;
   c.cap = P.cap;
   c.horizon = P.horizon;
   c.lam = P.lambda;
@@ -1014,6 +1014,95 @@ __global__ void __launch_bounds__(kMaxThreads, 1) tabu_kernel(const __grid_const
   if (C > 1 && looped) cluster_sync_all();
 }
 
+template <bool PEN, bool DL, bool DEBUG>
+__global__ void __launch_bounds__(kMaxThreads, 1) tabu_kernel(const __grid_constant__ KParams P) {
+  const int C = P.cluster;
+  const int rank = C > 1 ? static_cast<int>(cluster_rank()) : 0;
+  solve_one<PEN, DL, DEBUG>(P, P.lay, C, rank);
+}
+
+// ------------------------------------------------------------------ batches --------
+
+// Many instances in one launch. Instance b's arrays start at its offsets in the
+// concatenated inputs; outputs are concatenated the same way. work[0] is a queue
+// ticket counter (zeroed by batch_order_kernel), work[1 + k] the k-th instance to
+// solve (largest first).
+struct BParams {
+  KParams run;  // tenure, iterations, lambda, nt, timeout; no instance pointers
+  int32_t B;
+  const int32_t* loc_off;
+  const int32_t* veh_off;
+  const int32_t* mis_off;
+  const int64_t* travel_off;
+  const int32_t* travel;
+  const int32_t* veh_base;
+  const int32_t* veh_type;
+  const int32_t* pickup;
+  const int32_t* delivery;
+  const int32_t* heli_only;
+  const int32_t* deadline;
+  const int32_t* duty_cap;
+  const int32_t* horizon;
+  int32_t* out_off;
+  int32_t* out_route;
+  int32_t* out_flight;
+  int32_t* out_over;
+  int32_t* info;
+  int32_t* work;
+};
+
+__host__ __device__ inline int64_t moves_of(int64_t M, int64_t V) { return M * (M + V - 2) + M * (M - 1) / 2; }
+
+// Processing order: instances by decreasing neighbourhood size (ties by index), so the
+// persistent CTAs start the longest solves first. Also resets the ticket counter.
+__global__ void batch_order_kernel(int32_t B, const int32_t* veh_off, const int32_t* mis_off, int32_t* work) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+    const int64_t nb = moves_of(mis_off[b + 1] - mis_off[b], veh_off[b + 1] - veh_off[b]);
+    int r = 0;
+    for (int k = 0; k < B; ++k) {
+      const int64_t nk = moves_of(mis_off[k + 1] - mis_off[k], veh_off[k + 1] - veh_off[k]);
+      r += (nk > nb) || (nk == nb && k < b);
+    }
+    work[1 + r] = b;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) work[0] = 0;
+}
+
+template <bool PEN, bool DL>
+__global__ void __launch_bounds__(kMaxThreads, 1) tabu_batch_kernel(const __grid_constant__ BParams Q) {
+  __shared__ int s_ticket;
+  while (true) {
+    if (threadIdx.x == 0) s_ticket = atomicAdd(&Q.work[0], 1);
+    __syncthreads();
+    const int k = s_ticket;
+    __syncthreads();
+    if (k >= Q.B) break;
+    const int b = Q.work[1 + k];
+    KParams P = Q.run;
+    const int lo = Q.loc_off[b], vo = Q.veh_off[b], mo = Q.mis_off[b];
+    P.L = Q.loc_off[b + 1] - lo;
+    P.V = Q.veh_off[b + 1] - vo;
+    P.M = Q.mis_off[b + 1] - mo;
+    P.travel = Q.travel + Q.travel_off[b];
+    P.veh_base = Q.veh_base + vo;
+    P.veh_type = Q.veh_type ? Q.veh_type + vo : nullptr;
+    P.pickup = Q.pickup + mo;
+    P.delivery = Q.delivery + mo;
+    P.heli_only = Q.heli_only ? Q.heli_only + mo : nullptr;
+    P.deadline = Q.deadline ? Q.deadline + mo : nullptr;
+    P.cap = Q.duty_cap[b];
+    P.horizon = Q.horizon[b];
+    P.out_off = Q.out_off + vo + b;
+    P.out_route = Q.out_route + mo;
+    P.out_flight = Q.out_flight + vo;
+    P.out_over = Q.out_over + vo;
+    P.info = Q.info + static_cast<int64_t>(b) * ASCHED_INFO_LEN;
+    const Layout lay = make_layout(P.M, P.V, P.L, P.nt);
+    solve_one<PEN, DL, false>(P, lay, 1, 0);
+    __syncthreads();  // the next instance's prologue reuses shared memory
+  }
+}
+
 // ------------------------------------------------------------------ host side ------
 
 template <bool PEN, bool DL, bool DEBUG>
@@ -1049,7 +1138,6 @@ int check_sizes(const asched_instance* inst, const asched_params* p) {
   return ASCHED_OK;
 }
 
-int64_t moves_of(int64_t M, int64_t V) { return M * (M + V - 2) + M * (M - 1) / 2; }
 
 int max_smem_optin() {
   int dev = 0, v = 0;
@@ -1152,6 +1240,98 @@ int launch(const asched_instance* inst, const asched_params* p, bool debug, KPar
   return ASCHED_OK;
 }
 
+template <bool PEN, bool DL>
+void* batch_kernel_ptr() {
+  return reinterpret_cast<void*>(&tabu_batch_kernel<PEN, DL>);
+}
+
+int launch_batch(const asched_batch* bt, const asched_params* p, const asched_batch_result* out,
+                 void* workspace, size_t ws_bytes, void* stream) {
+  if (!bt || !p || !out) return ASCHED_E_INVALID;
+  const int B = bt->n_instances;
+  if (B < 0) return ASCHED_E_INVALID;
+  if (B == 0) return ASCHED_OK;
+  if (!bt->h_loc_off || !bt->h_veh_off || !bt->h_mis_off || !bt->loc_off || !bt->veh_off || !bt->mis_off ||
+      !bt->travel_off || !bt->travel || !bt->veh_base || !bt->pickup || !bt->delivery || !bt->duty_cap ||
+      !bt->horizon)
+    return ASCHED_E_INVALID;
+  if (!out->route_off || !out->route || !out->info || !workspace) return ASCHED_E_INVALID;
+  if (ws_bytes < sizeof(int32_t) * (static_cast<size_t>(B) + 1)) return ASCHED_E_INVALID;
+  if (p->cluster_size > 1) return ASCHED_E_INVALID;  // one CTA per instance in a batch
+  const int limit = max_smem_optin();
+  if (limit < 0) return ASCHED_E_CUDA;
+  int max_words = 0;
+  asched_instance one = {};
+  one.n_types = bt->n_types;
+  one.duty_cap = 0;
+  one.horizon = 0;
+  for (int b = 0; b < B; ++b) {
+    one.n_loc = bt->h_loc_off[b + 1] - bt->h_loc_off[b];
+    one.n_vehicles = bt->h_veh_off[b + 1] - bt->h_veh_off[b];
+    one.n_missions = bt->h_mis_off[b + 1] - bt->h_mis_off[b];
+    const int rc = check_sizes(&one, p);
+    if (rc != ASCHED_OK) return rc;
+    const Layout lay = make_layout(one.n_missions, one.n_vehicles, one.n_loc, one.n_types);
+    if (lay.total > max_words) max_words = lay.total;
+  }
+  const int64_t bytes = static_cast<int64_t>(max_words) * 4;
+  if (bytes + 64 > limit) return ASCHED_E_TOO_LARGE;
+  const bool pen = p->cap_mode == ASCHED_PENALTY;
+  const bool dl = bt->deadline != nullptr;
+  void* fn = pen ? (dl ? batch_kernel_ptr<true, true>() : batch_kernel_ptr<true, false>())
+                 : (dl ? batch_kernel_ptr<false, true>() : batch_kernel_ptr<false, false>());
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)) !=
+      cudaSuccess)
+    return ASCHED_E_CUDA;
+  const int threads = p->block_threads ? p->block_threads : kMaxThreads;
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, static_cast<size_t>(bytes)) !=
+          cudaSuccess) {
+    (void)cudaGetLastError();
+    return ASCHED_E_CUDA;
+  }
+  if (per_sm < 1) return ASCHED_E_TOO_LARGE;
+  const int grid = B < sms * per_sm ? B : sms * per_sm;
+  BParams q = {};
+  q.run.nt = bt->n_types;
+  q.run.tenure = p->tenure;
+  q.run.iterations = p->iterations;
+  q.run.lambda = pen ? p->lambda : 0;
+  q.run.cluster = 1;
+  q.run.timeout_ns = p->timeout_ns > 0 ? p->timeout_ns : kDefaultTimeoutNs;
+  q.B = B;
+  q.loc_off = bt->loc_off;
+  q.veh_off = bt->veh_off;
+  q.mis_off = bt->mis_off;
+  q.travel_off = bt->travel_off;
+  q.travel = bt->travel;
+  q.veh_base = bt->veh_base;
+  q.veh_type = bt->veh_type;
+  q.pickup = bt->pickup;
+  q.delivery = bt->delivery;
+  q.heli_only = bt->heli_only;
+  q.deadline = bt->deadline;
+  q.duty_cap = bt->duty_cap;
+  q.horizon = bt->horizon;
+  q.out_off = out->route_off;
+  q.out_route = out->route;
+  q.out_flight = out->flight;
+  q.out_over = out->overflow;
+  q.info = out->info;
+  q.work = static_cast<int32_t*>(workspace);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  batch_order_kernel<<<(B + 255) / 256, 256, 0, st>>>(B, bt->veh_off, bt->mis_off, q.work);
+  if (cudaGetLastError() != cudaSuccess) return ASCHED_E_CUDA;
+  void* args[] = {&q};
+  if (cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, static_cast<size_t>(bytes), st) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return ASCHED_E_CUDA;
+  }
+  return ASCHED_OK;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ C ABI ----------
@@ -1225,6 +1405,17 @@ int asched_solve(const asched_instance* inst, const asched_params* params, const
   kp.traj_move = out->traj_move;
   kp.traj_z = out->traj_z;
   return launch(inst, params, false, kp, stream);
+}
+
+int asched_batch_workspace_bytes(int32_t n_instances, size_t* out) {
+  if (!out || n_instances < 0) return ASCHED_E_INVALID;
+  *out = sizeof(int32_t) * (static_cast<size_t>(n_instances) + 1);
+  return ASCHED_OK;
+}
+
+int asched_solve_batch(const asched_batch* batch, const asched_params* params, const asched_batch_result* out,
+                       void* workspace, size_t workspace_bytes, void* stream) {
+  return launch_batch(batch, params, out, workspace, workspace_bytes, stream);
 }
 
 int asched_eval_neighbourhood(const asched_instance* inst, const asched_params* params,

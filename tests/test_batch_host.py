@@ -1,0 +1,46 @@
+"""Batch packing (host side, no GPU): concatenated arrays and offsets."""
+import numpy as np
+import pytest
+
+from paper_2002_11710_gb300 import api, gen
+
+
+def test_pack_offsets_and_contents():
+    insts = [gen.random_instance(s, n_loc=5 + s, n_vehicles=1 + s % 3, n_missions=3 * s,
+                                 n_types=2, heli_only_frac=0.3 if s % 2 else 0.0)
+             for s in range(5)]
+    bp = api.BatchProblem(insts, device="cpu")
+    assert bp.B == 5 and bp.n_types == 2
+    np.testing.assert_array_equal(bp.h_loc_off, np.cumsum([0] + [5 + s for s in range(5)]))
+    np.testing.assert_array_equal(bp.h_mis_off, np.cumsum([0] + [3 * s for s in range(5)]))
+    for b, inst in enumerate(insts):
+        vo, mo = bp.h_veh_off[b], bp.h_mis_off[b]
+        L = inst.n_loc
+        t0 = int(bp.h_travel_off[b])
+        np.testing.assert_array_equal(bp.travel[t0:t0 + 2 * L * L].numpy(), inst.travel.reshape(-1))
+        np.testing.assert_array_equal(bp.veh_base[vo:vo + inst.n_vehicles].numpy(), inst.veh_base)
+        np.testing.assert_array_equal(bp.pickup[mo:mo + inst.n_missions].numpy(), inst.pickup)
+        h = inst.heli_only if inst.heli_only is not None else np.zeros(inst.n_missions)
+        np.testing.assert_array_equal(bp.heli_only[mo:mo + inst.n_missions].numpy(), h)
+    out = bp.alloc_output()
+    assert out.route_off.numel() == bp.h_veh_off[-1] + bp.B
+    assert out.info.numel() == 5 * api.INFO_LEN
+
+
+def test_pack_rejects_mixed_layers_and_deadlines():
+    a = gen.random_instance(1, n_loc=5, n_vehicles=2, n_missions=4, n_types=1)
+    b = gen.random_instance(2, n_loc=5, n_vehicles=2, n_missions=4, n_types=2)
+    with pytest.raises(ValueError):
+        api.BatchProblem([a, b], device="cpu")
+    c = gen.random_instance(3, n_loc=5, n_vehicles=2, n_missions=4, deadlines=True)
+    with pytest.raises(ValueError):
+        api.BatchProblem([a, c], device="cpu")
+
+
+def test_workload_batches_pack():
+    for insts in ([gen.batched_member(i) for i in range(64)],
+                  [gen.random_instance(300 + s, n_loc=8, n_vehicles=3, n_missions=10, n_types=2)
+                   for s in range(3)] + [gen.random_instance(9, n_loc=30, n_vehicles=6, n_missions=90,
+                                                             n_types=2)]):
+        bp = api.BatchProblem(insts, device="cpu")
+        assert bp.B == len(insts)
