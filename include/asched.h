@@ -269,6 +269,28 @@ int asched_solve_batch(const asched_batch* batch, const asched_params* params,
                        const asched_batch_result* out, void* workspace, size_t workspace_bytes,
                        void* stream);
 
+/* Largest batch asched_solve_batch_static accepts. */
+#define ASCHED_STATIC_BATCH_MAX 16384
+
+/* asched_solve_batch without a caller workspace (no counterpart in the paper: it only
+ * changes who provides scratch memory). For callers that cannot allocate device memory
+ * themselves: a host program that embeds the solver with no device allocator of its
+ * own, or a dispatch loop that must not call cudaMalloc because cudaMalloc can
+ * synchronise the whole device and stall every other stream. The call allocates
+ * nothing: its queue counter and processing order live in a fixed array of
+ * 4 * (ASCHED_STATIC_BATCH_MAX + 1) bytes (64 KB) that every GPU using this library
+ * holds until the process exits. The caller still provides every input and output.
+ *   - Batches above ASCHED_STATIC_BATCH_MAX instances return ASCHED_E_TOO_LARGE.
+ *   - The first call on each device looks up the array's device address; make that
+ *     first call before any stream capture on that device.
+ *   - All calls on a device share the array and leave their contents in it (the next
+ *     call resets what must start at zero), so two of these calls whose work overlaps
+ *     on the GPU (different streams, not ordered) race with each other. Order them on
+ *     one stream, or use asched_solve_batch with separate workspaces.
+ * Results are those of asched_solve_batch. */
+int asched_solve_batch_static(const asched_batch* batch, const asched_params* params,
+                              const asched_batch_result* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

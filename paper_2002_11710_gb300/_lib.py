@@ -19,6 +19,8 @@ E_INFEASIBLE_INIT = -4
 E_TIMEOUT = -5
 E_CUDA = -6
 
+STATIC_BATCH_MAX = 16384  # ASCHED_STATIC_BATCH_MAX
+
 HARD = 0
 PENALTY = 1
 
@@ -81,6 +83,7 @@ SIGNATURES = {
                                                  P, P, P, P, P, P]),
     "asched_batch_workspace_bytes": (ctypes.c_int, [ctypes.c_int32, P]),
     "asched_solve_batch": (ctypes.c_int, [P, P, P, P, ctypes.c_size_t, P]),
+    "asched_solve_batch_static": (ctypes.c_int, [P, P, P, P]),
 }
 
 _lock = threading.Lock()

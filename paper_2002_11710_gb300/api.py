@@ -371,3 +371,19 @@ def autotune_batch(bp: BatchProblem, params: _lib.Params, candidates=(512, 384, 
             best = ms if best is None else min(best, ms)
         times[int(thr)] = best
     return min(times, key=times.get), times
+
+
+def solve_batch_static(bp: BatchProblem, params: _lib.Params, out: Optional[BatchOutput] = None,
+                       stream: Optional[torch.cuda.Stream] = None) -> BatchOutput:
+    """Queue asched_solve_batch_static: the same solve as solve_batch, for callers that
+    cannot provide device scratch memory; the library's fixed per-device array serves as
+    the work queue instead of bp.workspace. Calls that overlap on the GPU race on that
+    array, so keep them on one stream."""
+    if out is None:
+        out = bp.alloc_output()
+    s = stream if stream is not None else torch.cuda.current_stream(bp.device)
+    res = out.struct()
+    rc = _lib.load().asched_solve_batch_static(ctypes.byref(bp.struct), ctypes.byref(params),
+                                               ctypes.byref(res), ctypes.c_void_p(s.cuda_stream))
+    _lib.check(rc, "asched_solve_batch_static")
+    return out

@@ -33,6 +33,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "asched.h"
 
 namespace {
@@ -1334,6 +1336,39 @@ int launch_batch(const asched_batch* bt, const asched_params* p, const asched_ba
 
 }  // namespace
 
+// ------------------------------------------------------------------ fixed scratch ---
+
+// Work queue and processing order for asched_solve_batch_static: a fixed array in
+// every device's global memory, so that call needs no workspace from its caller.
+// Host code only uses its device address, looked up per device (see below).
+static __device__ __align__(256) int32_t g_batch_scratch[1 + ASCHED_STATIC_BATCH_MAX];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_batch_scratch on the current device, looked up on the first
+// call for that device.
+int static_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ASCHED_E_CUDA;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_batch_scratch) != cudaSuccess || !ptr) {
+      (void)cudaGetLastError();
+      return ASCHED_E_CUDA;
+    }
+    g_scratch_addr[dev] = ptr;
+  }
+  *out = g_scratch_addr[dev];
+  return ASCHED_OK;
+}
+
+}  // namespace
+
 // ------------------------------------------------------------------ C ABI ----------
 
 extern "C" {
@@ -1416,6 +1451,16 @@ int asched_batch_workspace_bytes(int32_t n_instances, size_t* out) {
 int asched_solve_batch(const asched_batch* batch, const asched_params* params, const asched_batch_result* out,
                        void* workspace, size_t workspace_bytes, void* stream) {
   return launch_batch(batch, params, out, workspace, workspace_bytes, stream);
+}
+
+int asched_solve_batch_static(const asched_batch* batch, const asched_params* params,
+                              const asched_batch_result* out, void* stream) {
+  if (!batch) return ASCHED_E_INVALID;
+  if (batch->n_instances > ASCHED_STATIC_BATCH_MAX) return ASCHED_E_TOO_LARGE;
+  void* scratch = nullptr;
+  const int rc = static_scratch(&scratch);
+  if (rc != ASCHED_OK) return rc;
+  return launch_batch(batch, params, out, scratch, sizeof(g_batch_scratch), stream);
 }
 
 int asched_eval_neighbourhood(const asched_instance* inst, const asched_params* params,
