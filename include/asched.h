@@ -116,7 +116,13 @@ typedef struct {
  *                       on it.
  *   block_threads       0 = automatic, else a multiple of 32 in [64, 512].
  *   timeout_ns          bound on every wait between CTAs; 0 = 1 s.
- *   flags               must be 0. */
+ *   flags               0, or ASCHED_COMPACT_LAYOUT.
+ * Shared-memory layout: instances whose location x mission gather tables fit in one
+ * CTA's shared memory use them; larger ones (or all, with ASCHED_COMPACT_LAYOUT) keep
+ * the travel matrix itself as int16 instead, which needs every travel time <= 32,767
+ * (else ASCHED_E_TOO_LARGE on the device) and iterations + tenure <= 32,767 (else
+ * ASCHED_E_TOO_LARGE from the call). Results do not depend on the layout. */
+#define ASCHED_COMPACT_LAYOUT 1u
 typedef struct {
   int32_t tenure;
   int32_t iterations;

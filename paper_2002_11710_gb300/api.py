@@ -14,7 +14,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (E_CUDA, E_INFEASIBLE_INIT, E_INVALID, E_OVERFLOW_GUARD, E_TIMEOUT,  # noqa: F401
+from ._lib import (COMPACT_LAYOUT, E_CUDA, E_INFEASIBLE_INIT, E_INVALID, E_OVERFLOW_GUARD, E_TIMEOUT,  # noqa: F401
                    E_TOO_LARGE, FLAG_ADMISSIBLE, FLAG_ASPIRATION, FLAG_FEASIBLE, FLAG_TABU, HARD,
                    INFO_BEST_IT, INFO_ITERS, INFO_LEN, INFO_STATUS, INFO_Z_BEST, INFO_Z_FINAL,
                    INFO_Z_INIT, NULL_MOVE, OK, PENALTY, SWAP_BIT, AschedError)
@@ -32,9 +32,12 @@ def num_moves(n_missions: int, n_vehicles: int) -> int:
 
 
 def make_params(tenure: int, iterations: int, cap_mode: int = HARD, lam: int = 1000,
-                cluster_size: int = 0, block_threads: int = 0, timeout_ns: int = 0) -> _lib.Params:
+                cluster_size: int = 0, block_threads: int = 0, timeout_ns: int = 0,
+                compact: bool = False) -> _lib.Params:
+    """compact: keep the travel matrix as int16 in shared memory instead of the gather
+    tables (used automatically when the tables do not fit)."""
     return _lib.Params(int(tenure), int(iterations), int(cap_mode), int(lam), int(cluster_size),
-                       int(block_threads), int(timeout_ns), 0)
+                       int(block_threads), int(timeout_ns), _lib.COMPACT_LAYOUT if compact else 0)
 
 
 def params_from(p, **overrides) -> _lib.Params:

@@ -62,24 +62,40 @@ constexpr int64_t kDefaultTimeoutNs = 1000000000ll;
 //   PRV[t] previous node; FB[v] flight of vehicle v minus the duty cap.
 constexpr int kBufWordsPerNode = 15;
 
+// Two table layouts. Small instances keep location x mission gather tables (int32):
+//   A[t][l][m] = T_t[l][p_m] + T_t[p_m][d_m],  B[t][l][m] = T_t[d_m][l],
+// row stride Mp words, so 32 lanes reading 32 consecutive missions hit 32 banks.
+// Large instances ("big") keep the travel matrix itself in int16 (exact while every
+// entry is below 2^15) with a row stride of Ls halves, Ls / 2 odd, so that random rows
+// and random columns both spread over the banks; tabu stamps are int16 there too.
 struct Layout {  // offsets in int32 words from the start of dynamic shared memory
   int A, B, tabu, cmat, wm, eloc, sloc, vtype, tyl, tym, st0, st1, best, order, cnt, gend, gdep, gfl,
       glast, misc, warpkey, slots, total;
-  int Mp, Np, Vp, buf;
+  int Mp, Np, Vp, buf, Ls;
+  bool big;
 };
 
 __host__ __device__ inline int round_up(int x, int k) { return (x + k - 1) / k * k; }
 
-__host__ __device__ inline Layout make_layout(int M, int V, int L, int nt) {
+__host__ __device__ inline Layout make_layout(int M, int V, int L, int nt, bool big) {
   Layout y;
+  y.big = big;
   y.Mp = round_up(M > 0 ? M : 1, 32);
   y.Np = round_up(M + V, 4);
   y.Vp = round_up(V, 4);
   y.buf = kBufWordsPerNode * y.Np + y.Vp;  // R2 Y4 S4 D4 PRV, then FB
+  y.Ls = round_up(L, 2);
+  if ((y.Ls / 2) % 2 == 0) y.Ls += 2;
   int o = 0;
-  y.A = o;       o += nt * L * y.Mp;
-  y.B = o;       o += nt * L * y.Mp;
-  y.tabu = o;    o += V * y.Mp;
+  if (big) {
+    y.A = o;     o += round_up(nt * L * y.Ls / 2, 4);  // int16 travel matrix
+    y.B = y.A;
+    y.tabu = o;  o += round_up(V * y.Mp / 2, 4);      // int16 stamps
+  } else {
+    y.A = o;     o += nt * L * y.Mp;
+    y.B = o;     o += nt * L * y.Mp;
+    y.tabu = o;  o += V * y.Mp;
+  }
   y.cmat = o;    o += nt * y.Mp;
   y.wm = o;      o += y.Mp;
   y.eloc = o;    o += y.Np;
@@ -271,6 +287,68 @@ struct Ctx {  // per-launch constants every thread keeps in registers
   int M, V, N, L, Mp, cap, horizon, lam;
 };
 
+// Table access for either layout. A row handle is (type offset + location) times the
+// row unit: Mp words for the gather tables, 1 (a row index) for the int16 matrix.
+template <bool BIG>
+struct Tab {
+  int A, B, tabu_off, cmat, eloc, sloc;
+  int Mp, L, Ls;
+  __device__ __forceinline__ int row(int tyl, int loc) const { return BIG ? tyl + loc : (tyl + loc) * Mp; }
+  __device__ __forceinline__ int t16(int i) const { return reinterpret_cast<const int16_t*>(g_smem + A)[i]; }
+  // A[row][m]: fly from the row's location to m's pickup, then m's own leg.
+  __device__ __forceinline__ int a(int r, int m) const {
+    if (BIG) return t16(r * Ls + g_smem[sloc + m]) + g_smem[cmat + (r >= L ? Mp : 0) + m];
+    return g_smem[A + r + m];
+  }
+  // B[row][m]: from m's delivery to the row's location.
+  __device__ __forceinline__ int b(int r, int m) const {
+    if (BIG) {
+      const int tyl = r >= L ? L : 0;
+      return t16((tyl + g_smem[eloc + m]) * Ls + (r - tyl));
+    }
+    return g_smem[B + r + m];
+  }
+  __device__ __forceinline__ int2 a2(int r, int m0) const {  // m0 even
+    if (BIG) return make_int2(a(r, m0), a(r, m0 + 1));
+    return *reinterpret_cast<const int2*>(g_smem + A + r + m0);
+  }
+  __device__ __forceinline__ int2 b2(int r, int m0) const {
+    if (BIG) return make_int2(b(r, m0), b(r, m0 + 1));
+    return *reinterpret_cast<const int2*>(g_smem + B + r + m0);
+  }
+  __device__ __forceinline__ int tabu(int v, int m) const {
+    if (BIG) return reinterpret_cast<const int16_t*>(g_smem + tabu_off)[v * Mp + m];
+    return g_smem[tabu_off + v * Mp + m];
+  }
+  __device__ __forceinline__ int2 tabu2(int v, int m0) const {  // m0 even
+    if (BIG) {
+      const short2 w = *reinterpret_cast<const short2*>(reinterpret_cast<const int16_t*>(g_smem + tabu_off) +
+                                                         v * Mp + m0);
+      return make_int2(w.x, w.y);
+    }
+    return *reinterpret_cast<const int2*>(g_smem + tabu_off + v * Mp + m0);
+  }
+  __device__ __forceinline__ void set_tabu(int v, int m, int x) const {
+    if (BIG) reinterpret_cast<int16_t*>(g_smem + tabu_off)[v * Mp + m] = static_cast<int16_t>(x);
+    else g_smem[tabu_off + v * Mp + m] = x;
+  }
+};
+
+template <bool BIG>
+__device__ __forceinline__ Tab<BIG> make_tab(const Layout& y, int L) {
+  Tab<BIG> t;
+  t.A = y.A;
+  t.B = y.B;
+  t.tabu_off = y.tabu;
+  t.cmat = y.cmat;
+  t.eloc = y.eloc;
+  t.sloc = y.sloc;
+  t.Mp = y.Mp;
+  t.L = L;
+  t.Ls = y.Ls;
+  return t;
+}
+
 constexpr int kNodeMask = 0x1FFF;  // next-node field of a node word
 __device__ __forceinline__ int nv_next(int nv) { return nv & kNodeMask; }
 __device__ __forceinline__ int nv_vw(int nv) { return (nv >> 13) & 0xFFF; }
@@ -282,24 +360,24 @@ __device__ __forceinline__ int vw_move(int from, int own) { return (from & 0x7FF
 
 // Write every record of node t into buffer S2 from its links (nx, pv), its vehicle
 // word vw and the flight f2 of that vehicle.
-template <bool PEN, bool DL>
-__device__ __forceinline__ void write_records(const Smem& sm, const State& S2, const Ctx& c, int t,
-                                              int nx, int pv, int vw, int f2) {
+template <bool PEN, bool DL, bool BIG>
+__device__ __forceinline__ void write_records(const Smem& sm, const Tab<BIG>& tb, const State& S2, const Ctx& c,
+                                              int t, int nx, int pv, int vw, int f2) {
   const int plane = vw_plane(vw);
   const int tyl = plane * c.L, tym = plane * c.Mp;
-  const int rowA = (tyl + sm.eloc[pv]) * c.Mp;
-  const int rowB = (tyl + sm.sloc[t]) * c.Mp;
+  const int rowA = tb.row(tyl, sm.eloc[pv]);
+  const int rowB = tb.row(tyl, sm.sloc[t]);
   const int nv = nx | (vw << 13);
   const int dep = (DL && pv < c.M) ? sm.wm[pv] : 0;
   S2.prv()[t] = pv;
   if (t < c.M) {
-    const int rowBn = (tyl + sm.sloc[nx]) * c.Mp;
-    const int aT = sm.A[rowA + t];
-    const int bT = sm.B[rowBn + t];
+    const int rowBn = tb.row(tyl, sm.sloc[nx]);
+    const int aT = tb.a(rowA, t);
+    const int bT = tb.b(rowBn, t);
     const int slot = aT + bT;
     const int ct = sm.cmat[tym + t];
     const int cn = nx < c.M ? sm.cmat[tym + nx] : 0;
-    const int leg = nx < c.M ? sm.A[rowA + nx] - cn : (pv < c.M ? sm.B[rowBn + pv] : 0);
+    const int leg = nx < c.M ? tb.a(rowA, nx) - cn : (pv < c.M ? tb.b(rowBn, pv) : 0);
     S2.r2()[t] = make_int2(nv, leg - slot);
     S2.y4()[t] = make_int4(rowA, rowB, aT - ct, nv);
     S2.s4()[t] = make_int4(nv, rowA, rowBn, slot);
@@ -308,7 +386,7 @@ __device__ __forceinline__ void write_records(const Smem& sm, const State& S2, c
       S2.d4()[t] = make_int4(dep, sm.wm[t] - ct, wn - cn, (dep + leg + cn <= wn) ? 1 : 0);
     }
   } else {
-    const int inleg = (pv == t) ? 0 : sm.B[rowB + pv];
+    const int inleg = (pv == t) ? 0 : tb.b(rowB, pv);
     S2.r2()[t] = make_int2(nv, 0);
     S2.y4()[t] = make_int4(rowA, rowB, inleg, nv);
     S2.s4()[t] = make_int4(nv, 0, 0, 0);
@@ -368,16 +446,16 @@ __device__ __forceinline__ uint64_t reloc_one(const Smem& sm, const State& S, co
 
 // Relocations of the mission pair (m0, m0 + 1), m0 even, before node y: every load
 // serves both (64-bit loads of consecutive table and record entries).
-template <bool PEN, bool DL, bool DEBUG>
-__device__ __forceinline__ uint64_t eval_relocate_pair(const Smem& sm, const State& S, const Ctx& c,
-                                                       int y, int m0, int it, int Z, int zbest,
+template <bool PEN, bool DL, bool DEBUG, bool BIG>
+__device__ __forceinline__ uint64_t eval_relocate_pair(const Smem& sm, const Tab<BIG>& tb, const State& S,
+                                                       const Ctx& c, int y, int m0, int it, int Z, int zbest,
                                                        const KParams& P) {
   const int4 rr = *reinterpret_cast<const int4*>(S.r2() + m0);  // {nv, rem} of m0 and m0 + 1
   const int4 g = S.y4()[y];  // A row, B row, leg into y, node word of y
   const int vy = nv_veh(g.w);
-  const int2 a2 = *reinterpret_cast<const int2*>(&sm.A[g.x + m0]);
-  const int2 b2 = *reinterpret_cast<const int2*>(&sm.B[g.y + m0]);
-  const int2 st = *reinterpret_cast<const int2*>(&sm.tabu[vy * c.Mp + m0]);
+  const int2 a2 = tb.a2(g.x, m0);
+  const int2 b2 = tb.b2(g.y, m0);
+  const int2 st = tb.tabu2(vy, m0);
   const int fy = S.fb()[vy];
   uint64_t k = reloc_one<PEN, DL, DEBUG>(sm, S, c, y, m0, rr.x, rr.y, g, a2.x, b2.x, fy, st.x, it, Z, zbest, P);
   if (m0 + 1 < c.M)
@@ -393,27 +471,29 @@ struct SwapParts {
   bool adjA, adjB;
 };
 
-__device__ __forceinline__ SwapParts swap_parts(const Smem& sm, const State& S, const Ctx& c, int a, int b) {
+template <bool BIG>
+__device__ __forceinline__ SwapParts swap_parts(const Smem& sm, const Tab<BIG>& tb, const State& S, const Ctx& c,
+                                                int a, int b) {
   SwapParts q;
   q.sa = S.s4()[a];
   q.sb = S.s4()[b];
   q.adjA = nv_next(q.sa.x) == b;  // a immediately before b
   q.adjB = nv_next(q.sb.x) == a;  // b immediately before a
   // A row of a mission's own delivery (needed only next to the other mission)
-  const int rowEa = q.adjB ? (vw_plane(nv_vw(q.sa.x)) * c.L + sm.eloc[a]) * c.Mp : 0;
-  const int rowEb = q.adjA ? (vw_plane(nv_vw(q.sb.x)) * c.L + sm.eloc[b]) * c.Mp : 0;
-  q.t1 = sm.A[(q.adjB ? rowEa : q.sa.y) + b];
-  q.t2 = sm.B[q.sa.z + (q.adjA ? a : b)];
-  q.t3 = sm.A[(q.adjA ? rowEb : q.sb.y) + a];
-  q.t4 = sm.B[q.sb.z + (q.adjB ? b : a)];
+  const int rowEa = q.adjB ? tb.row(vw_plane(nv_vw(q.sa.x)) * c.L, sm.eloc[a]) : 0;
+  const int rowEb = q.adjA ? tb.row(vw_plane(nv_vw(q.sb.x)) * c.L, sm.eloc[b]) : 0;
+  q.t1 = tb.a(q.adjB ? rowEa : q.sa.y, b);
+  q.t2 = tb.b(q.sa.z, q.adjA ? a : b);
+  q.t3 = tb.a(q.adjA ? rowEb : q.sb.y, a);
+  q.t4 = tb.b(q.sb.z, q.adjB ? b : a);
   return q;
 }
 
 // Swap S(a, b): the two missions exchange places.
-template <bool PEN, bool DL, bool DEBUG>
-__device__ __forceinline__ uint64_t eval_swap(const Smem& sm, const State& S, const Ctx& c, int a, int b,
-                                              int it, int Z, int zbest, const KParams& P) {
-  const SwapParts q = swap_parts(sm, S, c, a, b);
+template <bool PEN, bool DL, bool DEBUG, bool BIG>
+__device__ __forceinline__ uint64_t eval_swap(const Smem& sm, const Tab<BIG>& tb, const State& S, const Ctx& c,
+                                              int a, int b, int it, int Z, int zbest, const KParams& P) {
+  const SwapParts q = swap_parts<BIG>(sm, tb, S, c, a, b);
   const int nva = q.sa.x, nvb = q.sb.x;
   const int va = nv_veh(nva), vb = nv_veh(nvb);
   const int da = q.t1 + q.t2 - q.sa.w;
@@ -441,7 +521,7 @@ __device__ __forceinline__ uint64_t eval_swap(const Smem& sm, const State& S, co
     const bool l4 = q.adjB || (wa + q.t4 <= xb.z);
     feas = feas && l1 && l2 && l3 && l4;
   }
-  const bool tabu = (sm.tabu[vb * c.Mp + a] >= it) || (sm.tabu[va * c.Mp + b] >= it);
+  const bool tabu = (tb.tabu(vb, a) >= it) || (tb.tabu(va, b) >= it);
   const bool asp = Z + delta < zbest;
   const bool adm = feas && (!tabu || asp);
   const int m1 = a < b ? a : b, m2 = a < b ? b : a;
@@ -460,9 +540,10 @@ __device__ __forceinline__ uint64_t eval_swap(const Smem& sm, const State& S, co
 
 // One complete search (prologue, every iteration, epilogue) of the instance in P by
 // the C CTAs of this cluster (this CTA is `rank`), with shared memory laid out by lay.
-template <bool PEN, bool DL, bool DEBUG>
+template <bool PEN, bool DL, bool DEBUG, bool BIG>
 __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, const int C, const int rank) {
   const Smem sm = carve(lay);
+  const Tab<BIG> tb = make_tab<BIG>(lay, P.L);
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
   Ctx c;
@@ -513,6 +594,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
   maxT = __reduce_max_sync(0xffffffffu, maxT);
   if (lane == 0) atomicMax(&sm.misc[MISC_MAXT], maxT);
   if (__syncthreads_or(bad)) status = ASCHED_E_INVALID;
+  if (BIG && status == ASCHED_OK && sm.misc[MISC_MAXT] > 32767) status = ASCHED_E_TOO_LARGE;
   if (status == ASCHED_OK) {
     // 2 (2M + V + 2) maxT (1 + lambda) < 2^31 keeps every int32 sum in range.
     const double bound = 2.0 * (2.0 * M + V + 2.0) * static_cast<double>(sm.misc[MISC_MAXT]) *
@@ -523,18 +605,27 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
   // ---- prologue 2: gather tables, in-mission legs, tabu stamps, route ends
   const State S0 = sm.st(0);
   if (status == ASCHED_OK) {
-    for (int i = tid; i < nt * L * Mp; i += nthr) {
-      const int r = i / Mp, m = i - r * Mp;
-      const int t = r / L, l = r - t * L;
-      int av = 0, bv = 0;
-      if (m < M) {
-        const int32_t* T = P.travel + static_cast<int64_t>(t) * L * L;
-        const int p = sm.sloc[m], d = sm.eloc[m];
-        av = T[l * L + p] + T[p * L + d];
-        bv = T[d * L + l];
+    if (BIG) {
+      int16_t* T16 = reinterpret_cast<int16_t*>(g_smem + lay.A);
+      const int Ls = lay.Ls;
+      for (int i = tid; i < nt * L * Ls; i += nthr) {
+        const int r = i / Ls, j = i - r * Ls;
+        T16[i] = static_cast<int16_t>(j < L ? P.travel[static_cast<int64_t>(r) * L + j] : 0);
       }
-      sm.A[i] = av;
-      sm.B[i] = bv;
+    } else {
+      for (int i = tid; i < nt * L * Mp; i += nthr) {
+        const int r = i / Mp, m = i - r * Mp;
+        const int t = r / L, l = r - t * L;
+        int av = 0, bv = 0;
+        if (m < M) {
+          const int32_t* T = P.travel + static_cast<int64_t>(t) * L * L;
+          const int p = sm.sloc[m], d = sm.eloc[m];
+          av = T[l * L + p] + T[p * L + d];
+          bv = T[d * L + l];
+        }
+        sm.A[i] = av;
+        sm.B[i] = bv;
+      }
     }
     for (int i = tid; i < nt * Mp; i += nthr) {
       const int t = i / Mp, m = i - t * Mp;
@@ -547,7 +638,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
     }
     for (int i = tid; i < V * Mp; i += nthr) {
       const int v = i / Mp, m = i - v * Mp;
-      sm.tabu[i] = (P.tabu_in && m < M) ? P.tabu_in[static_cast<int64_t>(m) * V + v] : -1;
+      tb.set_tabu(v, m, (P.tabu_in && m < M) ? P.tabu_in[static_cast<int64_t>(m) * V + v] : -1);
     }
     for (int v = tid; v < V; v += nthr) {
       S0.nv(M + v) = (M + v) | ((v | ((sm.vtype[v] != 0 ? 1 : 0) << 10)) << 13);
@@ -619,10 +710,10 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
           for (int v = lane; v < V; v += 32) {
             const int tyl = sm.tyl[v];
             const int bl = sm.eloc[M + v];
-            const int a = sm.A[(tyl + sm.gend[v]) * Mp + m];
-            const int bret = sm.B[(tyl + bl) * Mp + m];
+            const int a = tb.a(tb.row(tyl, sm.gend[v]), m);
+            const int bret = tb.b(tb.row(tyl, bl), m);
             const int last = sm.glast[v];
-            const int old = last == M + v ? 0 : sm.B[(tyl + bl) * Mp + last];
+            const int old = last == M + v ? 0 : tb.b(tb.row(tyl, bl), last);
             const int app = a + bret - old;
             const int f = sm.gfl[v];
             bool ok = !(heli && sm.vtype[v] != 0);
@@ -646,9 +737,9 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
             const int tyl = sm.tyl[v];
             const int bl = sm.eloc[M + v];
             const int last = sm.glast[v];
-            const int a = sm.A[(tyl + sm.gend[v]) * Mp + m];
-            const int bret = sm.B[(tyl + bl) * Mp + m];
-            const int old = last == M + v ? 0 : sm.B[(tyl + bl) * Mp + last];
+            const int a = tb.a(tb.row(tyl, sm.gend[v]), m);
+            const int bret = tb.b(tb.row(tyl, bl), m);
+            const int old = last == M + v ? 0 : tb.b(tb.row(tyl, bl), last);
             S0.nv(last) = (S0.nv(last) & ~kNodeMask) | m;
             S0.prv()[m] = last;
             S0.nv(m) = (M + v) | ((nv_vw(S0.nv(M + v)) | (heli << 11)) << 13);
@@ -679,8 +770,8 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
       const int vw = nv_vw(S0.nv(t));
       const int tyl = vw_plane(vw) * L;
       int contrib;
-      if (t < M) contrib = sm.A[(tyl + sm.eloc[pv]) * Mp + t];
-      else contrib = pv == t ? 0 : sm.B[(tyl + sm.sloc[t]) * Mp + pv];
+      if (t < M) contrib = tb.a(tb.row(tyl, sm.eloc[pv]), t);
+      else contrib = pv == t ? 0 : tb.b(tb.row(tyl, sm.sloc[t]), pv);
       atomicAdd(&fl0[vw_veh(vw)], contrib);
     }
     __syncthreads();
@@ -690,16 +781,16 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
       const int vw = nv_vw(nv);
       const int f = fl0[vw_veh(vw)];
       const int tyl = vw_plane(vw) * L;
-      write_records<PEN, DL>(sm, S0, c, t, nv_next(nv), pv, vw, f);
+      write_records<PEN, DL, BIG>(sm, tb, S0, c, t, nv_next(nv), pv, vw, f);
       if (t < M) {
         infeasible |= (vw >> 11) & (vw >> 10) & 1;
         if (DL) {
           const int dep = pv < M ? sm.wm[pv] : 0;
-          infeasible |= dep + sm.A[(tyl + sm.eloc[pv]) * Mp + t] > sm.wm[t];
+          infeasible |= dep + tb.a(tb.row(tyl, sm.eloc[pv]), t) > sm.wm[t];
         }
       } else {
         if (!PEN) infeasible |= f > c.cap;
-        if (DL && pv != t) infeasible |= sm.wm[pv] + sm.B[(tyl + sm.sloc[t]) * Mp + pv] > c.horizon;
+        if (DL && pv != t) infeasible |= sm.wm[pv] + tb.b(tb.row(tyl, sm.sloc[t]), pv) > c.horizon;
       }
     }
     if (__syncthreads_or(infeasible)) status = ASCHED_E_INFEASIBLE_INIT;
@@ -758,7 +849,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
       const int zb_eval = DEBUG ? P.dbg_zbest : zbest;
       uint64_t key = kNoKey;
       for (int y = r_y, h = r_h; y < N;) {
-        key = min_u64(key, eval_relocate_pair<PEN, DL, DEBUG>(sm, S, c, y, 2 * h, it_eval, Z, zb_eval, P));
+        key = min_u64(key, eval_relocate_pair<PEN, DL, DEBUG, BIG>(sm, tb, S, c, y, 2 * h, it_eval, Z, zb_eval, P));
         h += Gr;
         y += Gq;
         if (h >= H) {
@@ -769,7 +860,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
       for (int j = s_j, row = s_row, a = s_a; j < Sn; j += G) {
         int b = a + row + 1;
         if (b >= M) b -= M;
-        key = min_u64(key, eval_swap<PEN, DL, DEBUG>(sm, S, c, a, b, it_eval, Z, zb_eval, P));
+        key = min_u64(key, eval_swap<PEN, DL, DEBUG, BIG>(sm, tb, S, c, a, b, it_eval, Z, zb_eval, P));
         a += Sr;
         row += Sq;
         if (a >= M) {
@@ -837,7 +928,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
             s = nv_next(r.x);
             e = S.prv()[m];
             x = S.prv()[y];
-            const int ins = sm.A[g.x + m] + sm.B[g.y + m] - g.z;
+            const int ins = tb.a(g.x, m) + tb.b(g.y, m) - g.z;
             const int fa = S.fb()[vw_veh(vwa)] + c.cap;
             if (vw_veh(vwa) == vw_veh(vwb)) {
               fa2 = fa + r.y + ins;
@@ -848,7 +939,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
           } else {
             a = static_cast<int>((id >> kIdShift) & kIdMask);
             b = static_cast<int>(id & kIdMask);
-            const SwapParts q = swap_parts(sm, S, c, a, b);
+            const SwapParts q = swap_parts<BIG>(sm, tb, S, c, a, b);
             vwa = nv_vw(q.sa.x);
             vwb = nv_vw(q.sb.x);
             na = nv_next(q.sa.x);
@@ -921,15 +1012,15 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
             }
             const int vv = vw_veh(vw);
             const int f2 = vv == va ? fa2 : (vv == vb ? fb2 : S.fb()[vv] + c.cap);
-            write_records<PEN, DL>(sm, S2, c, t, nx, pv, vw, f2);
+            write_records<PEN, DL, BIG>(sm, tb, S2, c, t, nx, pv, vw, f2);
             if (improved) sm.best[t] = nx;
           }
           if (tid == 0) {
             if (!is_swap) {
-              sm.tabu[va * Mp + m] = it + P.tenure;
+              tb.set_tabu(va, m, it + P.tenure);
             } else {
-              sm.tabu[va * Mp + a] = it + P.tenure;
-              sm.tabu[vb * Mp + b] = it + P.tenure;
+              tb.set_tabu(va, a, it + P.tenure);
+              tb.set_tabu(vb, b, it + P.tenure);
             }
           }
         }
@@ -1016,11 +1107,11 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
   if (C > 1 && looped) cluster_sync_all();
 }
 
-template <bool PEN, bool DL, bool DEBUG>
+template <bool PEN, bool DL, bool DEBUG, bool BIG>
 __global__ void __launch_bounds__(kMaxThreads, 1) tabu_kernel(const __grid_constant__ KParams P) {
   const int C = P.cluster;
   const int rank = C > 1 ? static_cast<int>(cluster_rank()) : 0;
-  solve_one<PEN, DL, DEBUG>(P, P.lay, C, rank);
+  solve_one<PEN, DL, DEBUG, BIG>(P, P.lay, C, rank);
 }
 
 // ------------------------------------------------------------------ batches --------
@@ -1032,6 +1123,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) tabu_kernel(const __grid_const
 struct BParams {
   KParams run;  // tenure, iterations, lambda, nt, timeout; no instance pointers
   int32_t B;
+  int32_t smem_words;  // dynamic shared memory of the launch
+  int32_t compact;     // always take the int16 matrix layout
   const int32_t* loc_off;
   const int32_t* veh_off;
   const int32_t* mis_off;
@@ -1099,26 +1192,50 @@ __global__ void __launch_bounds__(kMaxThreads, 1) tabu_batch_kernel(const __grid
     P.out_flight = Q.out_flight + vo;
     P.out_over = Q.out_over + vo;
     P.info = Q.info + static_cast<int64_t>(b) * ASCHED_INFO_LEN;
-    const Layout lay = make_layout(P.M, P.V, P.L, P.nt);
-    solve_one<PEN, DL, false>(P, lay, 1, 0);
+    // Each instance takes the gather tables when they fit the launch's shared
+    // memory, the int16 matrix otherwise.
+    const Layout small = make_layout(P.M, P.V, P.L, P.nt, false);
+    if (!Q.compact && small.total <= Q.smem_words) {
+      solve_one<PEN, DL, false, false>(P, small, 1, 0);
+    } else {
+      const Layout big = make_layout(P.M, P.V, P.L, P.nt, true);
+      solve_one<PEN, DL, false, true>(P, big, 1, 0);
+    }
     __syncthreads();  // the next instance's prologue reuses shared memory
   }
 }
 
 // ------------------------------------------------------------------ host side ------
 
-template <bool PEN, bool DL, bool DEBUG>
+template <bool PEN, bool DL, bool DEBUG, bool BIG>
 void* kernel_ptr() {
-  return reinterpret_cast<void*>(&tabu_kernel<PEN, DL, DEBUG>);
+  return reinterpret_cast<void*>(&tabu_kernel<PEN, DL, DEBUG, BIG>);
 }
 
-void* pick_kernel(bool pen, bool dl, bool debug) {
-  if (debug) {
-    if (pen) return dl ? kernel_ptr<true, true, true>() : kernel_ptr<true, false, true>();
-    return dl ? kernel_ptr<false, true, true>() : kernel_ptr<false, false, true>();
+template <bool DEBUG, bool BIG>
+void* pick_kernel_b(bool pen, bool dl) {
+  if (pen) return dl ? kernel_ptr<true, true, DEBUG, BIG>() : kernel_ptr<true, false, DEBUG, BIG>();
+  return dl ? kernel_ptr<false, true, DEBUG, BIG>() : kernel_ptr<false, false, DEBUG, BIG>();
+}
+
+void* pick_kernel(bool pen, bool dl, bool debug, bool big) {
+  if (debug) return big ? pick_kernel_b<true, true>(pen, dl) : pick_kernel_b<true, false>(pen, dl);
+  return big ? pick_kernel_b<false, true>(pen, dl) : pick_kernel_b<false, false>(pen, dl);
+}
+
+// Shared-memory layout for an instance: the gather tables when they fit, else the
+// int16 matrix (whose stamps limit iterations + tenure to 32,767).
+int choose_layout(int M, int V, int L, int nt, const asched_params* p, int limit_bytes, Layout* out) {
+  const Layout small = make_layout(M, V, L, nt, false);
+  if (!(p->flags & ASCHED_COMPACT_LAYOUT) && static_cast<int64_t>(small.total) * 4 + 64 <= limit_bytes) {
+    *out = small;
+    return ASCHED_OK;
   }
-  if (pen) return dl ? kernel_ptr<true, true, false>() : kernel_ptr<true, false, false>();
-  return dl ? kernel_ptr<false, true, false>() : kernel_ptr<false, false, false>();
+  const Layout big = make_layout(M, V, L, nt, true);
+  if (static_cast<int64_t>(big.total) * 4 + 64 > limit_bytes) return ASCHED_E_TOO_LARGE;
+  if (static_cast<int64_t>(p->iterations) + p->tenure > 32767) return ASCHED_E_TOO_LARGE;
+  *out = big;
+  return ASCHED_OK;
 }
 
 int check_sizes(const asched_instance* inst, const asched_params* p) {
@@ -1136,7 +1253,7 @@ int check_sizes(const asched_instance* inst, const asched_params* p) {
     return ASCHED_E_INVALID;
   if (p->block_threads != 0 && (p->block_threads < 64 || p->block_threads > kMaxThreads || p->block_threads % 32))
     return ASCHED_E_INVALID;
-  if (p->timeout_ns < 0 || p->flags != 0) return ASCHED_E_INVALID;
+  if (p->timeout_ns < 0 || (p->flags & ~ASCHED_COMPACT_LAYOUT) != 0) return ASCHED_E_INVALID;
   return ASCHED_OK;
 }
 
@@ -1153,11 +1270,12 @@ int make_plan(const asched_instance* inst, const asched_params* p, asched_plan_t
   int rc = check_sizes(inst, p);
   if (rc != ASCHED_OK) return rc;
   const int M = inst->n_missions, V = inst->n_vehicles;
-  const Layout lay = make_layout(M, V, inst->n_loc, inst->n_types);
-  const int64_t bytes = static_cast<int64_t>(lay.total) * 4;
   const int limit = max_smem_optin();
   if (limit < 0) return ASCHED_E_CUDA;
-  if (bytes > limit) return ASCHED_E_TOO_LARGE;
+  Layout lay;
+  rc = choose_layout(M, V, inst->n_loc, inst->n_types, p, limit, &lay);
+  if (rc != ASCHED_OK) return rc;
+  const int64_t bytes = static_cast<int64_t>(lay.total) * 4;
   const int64_t items = static_cast<int64_t>(M + V) * M + static_cast<int64_t>(M) * (M - 1) / 2;
   int threads = p->block_threads;
   if (threads == 0) {
@@ -1186,7 +1304,7 @@ int launch(const asched_instance* inst, const asched_params* p, bool debug, KPar
   if (inst->n_missions > 0 && (!inst->pickup || !inst->delivery)) return ASCHED_E_INVALID;
   const bool pen = p->cap_mode == ASCHED_PENALTY;
   const bool dl = inst->deadline != nullptr;
-  void* fn = pick_kernel(pen, dl, debug);
+  void* fn = pick_kernel(pen, dl, debug, lay.big);
   kp.travel = inst->travel;
   kp.veh_base = inst->veh_base;
   kp.veh_type = inst->veh_type;
@@ -1271,13 +1389,14 @@ int launch_batch(const asched_batch* bt, const asched_params* p, const asched_ba
     one.n_loc = bt->h_loc_off[b + 1] - bt->h_loc_off[b];
     one.n_vehicles = bt->h_veh_off[b + 1] - bt->h_veh_off[b];
     one.n_missions = bt->h_mis_off[b + 1] - bt->h_mis_off[b];
-    const int rc = check_sizes(&one, p);
+    int rc = check_sizes(&one, p);
     if (rc != ASCHED_OK) return rc;
-    const Layout lay = make_layout(one.n_missions, one.n_vehicles, one.n_loc, one.n_types);
+    Layout lay;
+    rc = choose_layout(one.n_missions, one.n_vehicles, one.n_loc, one.n_types, p, limit, &lay);
+    if (rc != ASCHED_OK) return rc;
     if (lay.total > max_words) max_words = lay.total;
   }
   const int64_t bytes = static_cast<int64_t>(max_words) * 4;
-  if (bytes + 64 > limit) return ASCHED_E_TOO_LARGE;
   const bool pen = p->cap_mode == ASCHED_PENALTY;
   const bool dl = bt->deadline != nullptr;
   void* fn = pen ? (dl ? batch_kernel_ptr<true, true>() : batch_kernel_ptr<true, false>())
@@ -1304,6 +1423,8 @@ int launch_batch(const asched_batch* bt, const asched_params* p, const asched_ba
   q.run.cluster = 1;
   q.run.timeout_ns = p->timeout_ns > 0 ? p->timeout_ns : kDefaultTimeoutNs;
   q.B = B;
+  q.smem_words = max_words;
+  q.compact = (p->flags & ASCHED_COMPACT_LAYOUT) ? 1 : 0;
   q.loc_off = bt->loc_off;
   q.veh_off = bt->veh_off;
   q.mis_off = bt->mis_off;

@@ -84,6 +84,10 @@ def test_check_instance_host_rejects_bad_params():
     assert api.check_instance_host(inst, _params(block_threads=100)) == api.E_INVALID
     assert api.check_instance_host(inst, _params(block_threads=1024)) == api.E_INVALID
     assert api.check_instance_host(inst, _params(cluster_size=16, block_threads=64)) == api.OK
+    assert api.check_instance_host(inst, _params(compact=True)) == api.OK
+    p = _params()
+    p.flags = 2
+    assert api.check_instance_host(inst, p) == api.E_INVALID
 
 
 def test_plan_without_a_device_reports_cuda_error():

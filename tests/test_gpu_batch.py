@@ -42,9 +42,10 @@ def _mixed_instances():
     return out
 
 
-def test_batch_members_equal_single_solves_and_oracle():
+@pytest.mark.parametrize("compact", [False, True], ids=["tables", "compact"])
+def test_batch_members_equal_single_solves_and_oracle(compact):
     insts = _mixed_instances()
-    params = api.make_params(5, 60, PENALTY, 1000)
+    params = api.make_params(5, 60, PENALTY, 1000, compact=compact)
     bp = api.BatchProblem(insts)
     out = api.solve_batch(bp, params)
     torch.cuda.synchronize()

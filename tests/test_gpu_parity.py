@@ -64,8 +64,9 @@ EVAL_CASES = [
 ]
 
 
+@pytest.mark.parametrize("compact", [False, True], ids=["tables", "compact"])
 @pytest.mark.parametrize("name,mk,mode,tenure", EVAL_CASES, ids=[c[0] for c in EVAL_CASES])
-def test_eval_neighbourhood_matches_oracle(name, mk, mode, tenure):
+def test_eval_neighbourhood_matches_oracle(name, mk, mode, tenure, compact):
     inst = mk()
     pb = oracle.Problem(inst, mode, 1000)
     rc, off0, route0 = oracle.greedy_init(pb)
@@ -73,7 +74,7 @@ def test_eval_neighbourhood_matches_oracle(name, mk, mode, tenure):
     iters = 30 if inst.n_missions < 50 else 6
     r = oracle.tabu_search(pb, tenure, iters)
     dp = api.DeviceProblem(inst)
-    params = api.make_params(tenure, 0, mode, 1000)
+    params = api.make_params(tenure, 0, mode, 1000, compact=compact)
     checked = 0
     for it, off, route, tabu, z, z_best in _replay_states(pb, tenure, r["traj_move"], (off0, route0)):
         if it % 3 and it != iters - 1:
@@ -147,9 +148,10 @@ def _check_solve_vs_oracle(inst, mode, tenure, iters, **launch):
     return gm, gz
 
 
+@pytest.mark.parametrize("compact", [False, True], ids=["tables", "compact"])
 @pytest.mark.parametrize("name,mk,mode,tenure,iters", TRAJ_CASES, ids=[c[0] for c in TRAJ_CASES])
-def test_solve_trajectory_matches_oracle(name, mk, mode, tenure, iters):
-    _check_solve_vs_oracle(mk(), mode, tenure, iters)
+def test_solve_trajectory_matches_oracle(name, mk, mode, tenure, iters, compact):
+    _check_solve_vs_oracle(mk(), mode, tenure, iters, compact=compact)
 
 
 @pytest.mark.parametrize("cluster,threads", [(1, 512), (2, 512), (4, 128), (8, 448), (16, 256)])
@@ -241,11 +243,40 @@ def test_paper_shaped_full_run_sampled_against_oracle():
     assert info[api.INFO_BEST_IT] == int(np.argmin(zs)) - 1
 
 
-def test_edge_sizes():
+@pytest.mark.parametrize("compact", [False, True], ids=["tables", "compact"])
+def test_edge_sizes(compact):
     for M, V in [(0, 3), (1, 1), (2, 1), (1, 5), (3, 2), (64, 1), (65, 2)]:
         inst = gen.random_instance(80 + M + V, n_loc=8, n_vehicles=V, n_missions=M,
                                    duty_cap=100000, max_minutes=50)
-        _check_solve_vs_oracle(inst, PENALTY, 3, 25)
+        _check_solve_vs_oracle(inst, PENALTY, 3, 25, compact=compact)
+
+
+def test_large_instance_sampled_against_oracle():
+    """The large configuration (400 missions, 50 vehicles, 240 locations) only fits in
+    the compact layout. Its first 120 iterations: every objective is recomputed by the
+    oracle from the replayed schedule and sampled iterations must choose the oracle's
+    move."""
+    inst, p = gen.large(0), gen.LARGE_PARAMS
+    iters = 120
+    dp = api.DeviceProblem(inst)
+    params = api.params_from(p, iterations=iters)
+    assert api.plan(dp, params).smem_bytes > 200 * 1024
+    out = api.solve(dp, params, trajectory=True)
+    torch.cuda.synchronize()
+    info = out.info.cpu().numpy()
+    assert info[api.INFO_STATUS] == 0 and info[api.INFO_ITERS] == iters
+    gm = out.traj_move.cpu().numpy().view(np.uint32)
+    gz = out.traj_z.cpu().numpy()
+    pb = oracle.Problem(inst, p.cap_mode, p.lam)
+    rc, off0, route0 = oracle.greedy_init(pb)
+    assert rc == 0 and info[api.INFO_Z_INIT] == oracle.cost(pb, off0, route0)[0]
+    sample = {0, 1, 59, iters - 1}
+    for it, off, route, tabu, z, zb in _replay_states(pb, p.tenure, gm, (off0, route0)):
+        if it in sample:
+            ids, delta, flags, chosen = oracle.eval_neighbourhood(pb, off, route, tabu, it, zb)
+            assert int(gm[it]) == (0xFFFFFFFF if chosen < 0 else int(ids[chosen])), f"iteration {it}"
+        if it > 0:
+            assert int(gz[it - 1]) == z, f"objective after iteration {it - 1}"
 
 
 def test_device_status_codes():
@@ -289,3 +320,12 @@ def test_host_side_errors():
     with pytest.raises(api.AschedError) as e:
         api.solve(api.DeviceProblem(huge), api.make_params(3, 5, PENALTY, 1))
     assert e.value.status == api.E_TOO_LARGE
+    # the compact layout's int16 stamps cap iterations + tenure
+    with pytest.raises(api.AschedError) as e:
+        api.solve(dp, api.make_params(3, 40000, PENALTY, 1000, compact=True))
+    assert e.value.status == api.E_TOO_LARGE
+    # travel times above int16 cannot use the compact layout
+    wide = gen.Instance(**{**base.__dict__, "travel": base.travel * 200})
+    out = api.solve(api.DeviceProblem(wide), api.make_params(3, 5, PENALTY, 1, compact=True))
+    torch.cuda.synchronize()
+    assert int(out.info[api.INFO_STATUS]) == api.E_TOO_LARGE
