@@ -247,6 +247,7 @@ def run_gpu(args, rank, world, local_rank):
     e2e_s = sum(e2e_times)
     e2e_s = max_over_ranks(e2e_s, world, dev)
     batched = run_batched(args, dev) if args.batched else None
+    serving = run_serving(args, dev) if args.serve_seconds > 0 else None
     if rank != 0:
         return
     value = whole_job_rate(moves_step * args.steps, world, dev_s)
@@ -287,6 +288,7 @@ def run_gpu(args, rank, world, local_rank):
                      "peak_basis": f"{sm_count} SMs x {int_lanes} int32 lanes/clk x {sm_max_mhz:.0f} MHz",
                      "frac_of_sms_used": achieved / (peak_tops * plan.cluster_size / sm_count)},
         "batched": batched,
+        "serving": serving,
         "cpu_baseline": None if cpu_rate is None else {
             "value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {args.cpu_iterations} of 5,000 iterations, same instance, {cpu_dt:.1f} s"},
@@ -343,6 +345,61 @@ def run_batched(args, dev):
             "speedup_vs_sequential": seq_ms / t, "gpu_launches": 2}
 
 
+def run_serving(args, dev):
+    """The serving workload: Poisson re-planning requests at 2,000 req/s (sizes
+    lognormal around 60 missions, clipped to [10, 400], V = ceil(M/5), 1,000 iterations
+    each) through the continuous-batching server, with slots admitted under a 40 GB
+    device-memory budget; against the plain path (one asched_solve launch per request,
+    in arrival order on one stream) for the first second of the same stream."""
+    import torch
+
+    from paper_2002_11710_gb300 import api, gen, serve
+
+    params = api.params_from(gen.SERVING_PARAMS)
+    pool = [gen.serving_request(20_000 + k) for k in range(2048)]
+    arrivals = gen.poisson_arrivals(7, 2000.0, args.serve_seconds)
+    reqs = [pool[k % len(pool)] for k in range(len(arrivals))]
+    srv = serve.Server(max_loc=72, max_vehicles=80, max_missions=400, n_slots=4096,
+                       budget_bytes=40 << 30, device=dev)
+    srv.start(params, idle_timeout_s=60.0)
+    try:
+        lat, wall = serve.run_stream(srv, reqs, arrivals)
+    finally:
+        srv.stop()
+    served = srv.served()
+    # plain per-request path on the first second of arrivals
+    n_plain = int((arrivals < 1.0).sum())
+    dps = [api.DeviceProblem(r, dev) for r in reqs[:n_plain]]
+    outs = [api.alloc_output(d, params.iterations) for d in dps]
+    torch.cuda.synchronize()
+    st = torch.cuda.Stream(device=dev)
+    evs = [torch.cuda.Event() for _ in range(n_plain)]
+    lat2 = np.zeros(n_plain)
+    t0 = time.perf_counter()
+    i = k = 0
+    while k < n_plain:
+        now = time.perf_counter() - t0
+        while i < n_plain and arrivals[i] <= now:
+            api.solve(dps[i], params, out=outs[i], stream=st)
+            evs[i].record(st)
+            i += 1
+        while k < i and evs[k].query():
+            lat2[k] = time.perf_counter() - t0 - arrivals[k]
+            k += 1
+    wall2 = time.perf_counter() - t0
+    return {"workload": (f"Poisson 2,000 req/s for {args.serve_seconds:g} s, M ~ lognormal(median 60) "
+                         "in [10, 400], V = ceil(M/5), 1,000 iterations, 40 GB slot budget"),
+            "requests": len(reqs), "served": served, "wall_s": wall,
+            "solves_per_s": len(reqs) / wall,
+            "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3),
+                           "p99": float(np.percentile(lat, 99) * 1e3),
+                           "max": float(lat.max() * 1e3)},
+            "slots": srv.n_slots, "slot_bytes": srv.slot_bytes,
+            "plain_per_request": {"requests": n_plain, "solves_per_s": n_plain / wall2,
+                                  "latency_ms": {"p50": float(np.percentile(lat2, 50) * 1e3),
+                                                 "p99": float(np.percentile(lat2, 99) * 1e3)}}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -356,6 +413,9 @@ def main():
     ap.add_argument("--int32-lanes-per-sm", type=int, default=128)
     ap.add_argument("--no-batched", dest="batched", action="store_false",
                     help="skip the 1,024-instance batched measurement")
+    ap.add_argument("--serve-seconds", type=float, default=20.0,
+                    help="length of the Poisson request stream for the serving measurement "
+                         "(the serving workload is 60 s; 0 skips it)")
     args = ap.parse_args()
     world = _env_int("WORLD_SIZE", 1)
     rank = _env_int("RANK", 0)

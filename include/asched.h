@@ -275,6 +275,68 @@ int asched_solve_batch(const asched_batch* batch, const asched_params* params,
                        const asched_batch_result* out, void* workspace, size_t workspace_bytes,
                        void* stream);
 
+/* ---------------------------------------------------------------- serving ----------
+ * A persistent launch that solves requests while the host keeps admitting new ones
+ * (continuous batching: every CTA takes the next published request as soon as it is
+ * free, so requests that arrive while others run overlap with them on the device).
+ *
+ * Device memory, all caller-owned:
+ *   slot_data [n_slots][slot_words]  request inputs; slot layout (int32 words):
+ *       [0] n_loc  [1] n_vehicles  [2] n_missions  [3] duty_cap  [4] horizon
+ *       [5] flags (1: heli_only present, 2: deadline present)  [6] sequence number
+ *       [ASCHED_SLOT_HEADER ...] travel [n_types][n_loc][n_loc] (row length n_loc),
+ *       then at ASCHED_SLOT_HEADER + n_types*max_loc^2: veh_base [max_vehicles],
+ *       veh_type [max_vehicles], pickup [max_missions], delivery [max_missions],
+ *       heli_only [max_missions], deadline [max_missions].
+ *   slot_out [n_slots][out_words]  results: route_off [max_vehicles + 1], route
+ *       [max_missions], flight [max_vehicles], overflow [max_vehicles], info
+ *       [ASCHED_INFO_LEN].
+ *   ring [ring_len]   slot index of ticket t at ring[t % ring_len] (ring_len >= n_slots).
+ *   control [ASCHED_CTRL_LEN]  zeroed before the launch; the host raises
+ *       control[ASCHED_CTRL_PUBLISHED] to publish tickets and sets
+ *       control[ASCHED_CTRL_STOP] to end the launch; the launch counts served requests
+ *       in control[ASCHED_CTRL_SERVED].
+ *   done [n_slots]    the launch writes slot s's sequence number there when s is solved.
+ * Publish a slot by copies ordered on one stream: slot contents, then its ring entry,
+ * then the new published count. A slot may be rewritten once its sequence number has
+ * appeared in done[]. Requests of one launch share asched_params, and either all or none
+ * carry deadlines (has_deadlines). */
+#define ASCHED_SLOT_HEADER 16
+#define ASCHED_CTRL_PUBLISHED 0
+#define ASCHED_CTRL_CLAIMED 1
+#define ASCHED_CTRL_STOP 2
+#define ASCHED_CTRL_SERVED 3
+#define ASCHED_CTRL_IDLE_EXITS 4
+#define ASCHED_CTRL_LEN 8
+
+typedef struct {
+  int32_t n_slots;
+  int32_t ring_len;
+  int32_t max_loc;
+  int32_t max_vehicles;
+  int32_t max_missions;
+  int32_t n_types;
+  int32_t has_deadlines;
+  int32_t* slot_data;
+  int32_t* slot_out;
+  int32_t* ring;
+  int32_t* control;
+  int32_t* done;
+} asched_server;
+
+/* Words per input slot and per output slot for the given capacities. Host only. */
+int asched_server_sizes(int32_t max_loc, int32_t max_vehicles, int32_t max_missions, int32_t n_types,
+                        int32_t* slot_words, int32_t* out_words);
+
+/* Start the serving launch on `stream` (returns at once). max_ctas > 0 caps the number
+ * of CTAs (default: every SM). The launch ends once control[ASCHED_CTRL_STOP] is set and
+ * every published request has been taken, or after idle_timeout_ns (> 0) without a new
+ * request (counted in control[ASCHED_CTRL_IDLE_EXITS]). A request whose sizes exceed the
+ * capacities, or whose deadline flag differs from has_deadlines, gets ASCHED_E_INVALID
+ * in its info[ASCHED_INFO_STATUS]. */
+int asched_serve(const asched_server* server, const asched_params* params, int64_t idle_timeout_ns,
+                 int32_t max_ctas, void* stream);
+
 /* Largest batch asched_solve_batch_static accepts. */
 #define ASCHED_STATIC_BATCH_MAX 16384
 

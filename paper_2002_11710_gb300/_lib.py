@@ -60,6 +60,19 @@ class Result(ctypes.Structure):
                 ("traj_move", P), ("traj_z", P)]
 
 
+class Server(ctypes.Structure):
+    _fields_ = [("n_slots", ctypes.c_int32), ("ring_len", ctypes.c_int32),
+                ("max_loc", ctypes.c_int32), ("max_vehicles", ctypes.c_int32),
+                ("max_missions", ctypes.c_int32), ("n_types", ctypes.c_int32),
+                ("has_deadlines", ctypes.c_int32), ("slot_data", P), ("slot_out", P),
+                ("ring", P), ("control", P), ("done", P)]
+
+
+SLOT_HEADER = 16
+CTRL_PUBLISHED, CTRL_CLAIMED, CTRL_STOP, CTRL_SERVED, CTRL_IDLE_EXITS = 0, 1, 2, 3, 4
+CTRL_LEN = 8
+
+
 class Batch(ctypes.Structure):
     _fields_ = [("n_instances", ctypes.c_int32), ("n_types", ctypes.c_int32),
                 ("h_loc_off", P), ("h_veh_off", P), ("h_mis_off", P),
@@ -85,6 +98,9 @@ SIGNATURES = {
     "asched_batch_workspace_bytes": (ctypes.c_int, [ctypes.c_int32, P]),
     "asched_solve_batch": (ctypes.c_int, [P, P, P, P, ctypes.c_size_t, P]),
     "asched_solve_batch_static": (ctypes.c_int, [P, P, P, P]),
+    "asched_server_sizes": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_int32, P, P]),
+    "asched_serve": (ctypes.c_int, [P, P, ctypes.c_int64, ctypes.c_int32, P]),
 }
 
 _lock = threading.Lock()

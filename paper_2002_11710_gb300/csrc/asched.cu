@@ -186,6 +186,11 @@ __device__ __forceinline__ uint64_t ld_own_u64(uint32_t cta_addr) {
   return v;
 }
 
+// Instance inputs are read through L2 only (ld.global.cg): a persistent launch reuses
+// request slots whose new contents arrive by copy while it runs, and L1 is not kept
+// coherent with those writes. These reads happen outside the iteration loop.
+__device__ __forceinline__ int gin(const int32_t* p) { return __ldcg(p); }
+
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -564,10 +569,10 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
   int bad = 0;
   for (int i = tid; i < Mp; i += nthr) {
     if (i < M) {
-      const int p = P.pickup[i], d = P.delivery[i];
-      const int h = P.heli_only ? P.heli_only[i] : 0;
+      const int p = gin(P.pickup + i), d = gin(P.delivery + i);
+      const int h = P.heli_only ? gin(P.heli_only + i) : 0;
       bad |= (p < 0) | (p >= L) | (d < 0) | (d >= L) | (p == d) | (h < 0) | (h > 1);
-      sm.wm[i] = P.deadline ? P.deadline[i] : 0;
+      sm.wm[i] = P.deadline ? gin(P.deadline + i) : 0;
       sm.eloc[i] = d;
       sm.sloc[i] = p;
       sm.cnt[i] = 0;
@@ -576,8 +581,8 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
     }
   }
   for (int v = tid; v < V; v += nthr) {
-    const int b = P.veh_base[v];
-    const int ty = P.veh_type ? P.veh_type[v] : 0;
+    const int b = gin(P.veh_base + v);
+    const int ty = P.veh_type ? gin(P.veh_type + v) : 0;
     bad |= (b < 0) | (b >= L) | (ty < 0) | (ty >= nt);
     sm.eloc[M + v] = b;
     sm.sloc[M + v] = b;
@@ -587,7 +592,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
   }
   int maxT = 0;
   for (int i = tid; i < nt * L * L; i += nthr) {
-    const int x = P.travel[i];
+    const int x = gin(P.travel + i);
     bad |= x < 0;
     maxT = x > maxT ? x : maxT;
   }
@@ -610,7 +615,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
       const int Ls = lay.Ls;
       for (int i = tid; i < nt * L * Ls; i += nthr) {
         const int r = i / Ls, j = i - r * Ls;
-        T16[i] = static_cast<int16_t>(j < L ? P.travel[static_cast<int64_t>(r) * L + j] : 0);
+        T16[i] = static_cast<int16_t>(j < L ? gin(P.travel + static_cast<int64_t>(r) * L + j) : 0);
       }
     } else {
       for (int i = tid; i < nt * L * Mp; i += nthr) {
@@ -620,8 +625,8 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
         if (m < M) {
           const int32_t* T = P.travel + static_cast<int64_t>(t) * L * L;
           const int p = sm.sloc[m], d = sm.eloc[m];
-          av = T[l * L + p] + T[p * L + d];
-          bv = T[d * L + l];
+          av = gin(T + l * L + p) + gin(T + p * L + d);
+          bv = gin(T + d * L + l);
         }
         sm.A[i] = av;
         sm.B[i] = bv;
@@ -632,13 +637,13 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
       int cv = 0;
       if (m < M) {
         const int32_t* T = P.travel + static_cast<int64_t>(t) * L * L;
-        cv = T[sm.sloc[m] * L + sm.eloc[m]];
+        cv = gin(T + sm.sloc[m] * L + sm.eloc[m]);
       }
       sm.cmat[i] = cv;
     }
     for (int i = tid; i < V * Mp; i += nthr) {
       const int v = i / Mp, m = i - v * Mp;
-      tb.set_tabu(v, m, (P.tabu_in && m < M) ? P.tabu_in[static_cast<int64_t>(m) * V + v] : -1);
+      tb.set_tabu(v, m, (P.tabu_in && m < M) ? gin(P.tabu_in + static_cast<int64_t>(m) * V + v) : -1);
     }
     for (int v = tid; v < V; v += nthr) {
       S0.nv(M + v) = (M + v) | ((v | ((sm.vtype[v] != 0 ? 1 : 0) << 10)) << 13);
@@ -652,7 +657,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
     if (P.init_off) {
       int csr_bad = 0;
       for (int v = tid; v < V; v += nthr) {
-        const int o0 = P.init_off[v], o1 = P.init_off[v + 1];
+        const int o0 = gin(P.init_off + v), o1 = gin(P.init_off + v + 1);
         if (o0 < 0 || o1 < o0 || o1 > M || (v == 0 && o0 != 0) || (v == V - 1 && o1 != M)) {
           csr_bad = 1;
           continue;
@@ -660,7 +665,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
         int prev = M + v;
         const int vw = nv_vw(S0.nv(M + v));
         for (int k = o0; k < o1; ++k) {
-          const int m = P.init_route[k];
+          const int m = gin(P.init_route + k);
           if (m < 0 || m >= M) {
             csr_bad = 1;
             break;
@@ -668,7 +673,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
           atomicAdd(&sm.cnt[m], 1);
           S0.nv(prev) = (S0.nv(prev) & ~kNodeMask) | m;
           S0.prv()[m] = prev;
-          S0.nv(m) = (vw | ((P.heli_only ? P.heli_only[m] : 0) << 11)) << 13;
+          S0.nv(m) = (vw | ((P.heli_only ? gin(P.heli_only + m) : 0) << 11)) << 13;
           prev = m;
         }
         S0.nv(prev) = (S0.nv(prev) & ~kNodeMask) | (M + v);
@@ -684,10 +689,10 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
     } else {
       // Mission order: heli-only first, then by deadline, then by id.
       for (int m = tid; m < M; m += nthr) {
-        const int hm = (P.heli_only && P.heli_only[m]) ? 0 : 1, wmv = DL ? sm.wm[m] : 0;
+        const int hm = (P.heli_only && gin(P.heli_only + m)) ? 0 : 1, wmv = DL ? sm.wm[m] : 0;
         int r = 0;
         for (int k = 0; k < M; ++k) {
-          const int hk = (P.heli_only && P.heli_only[k]) ? 0 : 1, wk = DL ? sm.wm[k] : 0;
+          const int hk = (P.heli_only && gin(P.heli_only + k)) ? 0 : 1, wk = DL ? sm.wm[k] : 0;
           r += (hk < hm) || (hk == hm && (wk < wmv || (wk == wmv && k < m)));
         }
         sm.order[r] = m;
@@ -705,7 +710,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
         for (int k = 0; k < M && !fail; ++k) {
           const int m = sm.order[k];
           const int w = sm.wm[m];
-          const int heli = P.heli_only ? P.heli_only[m] : 0;
+          const int heli = P.heli_only ? gin(P.heli_only + m) : 0;
           uint64_t best = kNoKey;
           for (int v = lane; v < V; v += 32) {
             const int tyl = sm.tyl[v];
@@ -1081,11 +1086,11 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
         int f = 0, prevloc = bl, t = sm.best[M + v];
         while (t != M + v) {
           P.out_route[o++] = t;
-          f += T[prevloc * L + sm.sloc[t]] + T[sm.sloc[t] * L + sm.eloc[t]];
+          f += gin(T + prevloc * L + sm.sloc[t]) + gin(T + sm.sloc[t] * L + sm.eloc[t]);
           prevloc = sm.eloc[t];
           t = sm.best[t];
         }
-        if (lens[v] > 0) f += T[prevloc * L + bl];
+        if (lens[v] > 0) f += gin(T + prevloc * L + bl);
         if (P.out_flight) P.out_flight[v] = f;
         if (P.out_over) P.out_over[v] = pos0(f - c.cap);
       }
@@ -1202,6 +1207,121 @@ __global__ void __launch_bounds__(kMaxThreads, 1) tabu_batch_kernel(const __grid
       solve_one<PEN, DL, false, true>(P, big, 1, 0);
     }
     __syncthreads();  // the next instance's prologue reuses shared memory
+  }
+}
+
+// ------------------------------------------------------------------ serving --------
+
+// A persistent launch that serves requests as the host publishes them. Each request
+// sits in a fixed-capacity slot (inputs) with a matching output slot; the host writes
+// a slot, appends its index to the ring and raises control[PUBLISHED], all by copies
+// ordered on one stream. A CTA takes the next ticket, solves that slot's instance with
+// the same per-instance search as asched_solve, and writes the request's sequence
+// number to done[slot]. Every wait is bounded: the launch ends when control[STOP] is
+// set and every published ticket is taken, or after idle_ns without a new ticket.
+struct SParams {
+  KParams run;
+  int32_t n_slots, ring_len, Lc, Vc, Mc, nt;
+  int32_t slot_words, out_words, smem_words, compact;
+  int64_t idle_ns;
+  const int32_t* slot_data;
+  int32_t* slot_out;
+  const int32_t* ring;
+  int32_t* control;
+  int32_t* done;
+};
+
+__host__ __device__ inline int serve_slot_words(int Lc, int Vc, int Mc, int nt) {
+  return round_up(ASCHED_SLOT_HEADER + nt * Lc * Lc + 2 * Vc + 4 * Mc, 4);
+}
+__host__ __device__ inline int serve_out_words(int Vc, int Mc) {
+  return round_up(3 * Vc + 1 + Mc + ASCHED_INFO_LEN, 4);
+}
+
+__device__ __forceinline__ int ld_volatile_i32(const int32_t* p) { return *reinterpret_cast<const volatile int32_t*>(p); }
+
+template <bool PEN, bool DL>
+__global__ void __launch_bounds__(kMaxThreads, 1) serve_kernel(const __grid_constant__ SParams Q) {
+  __shared__ int s_ticket;
+  uint64_t idle_since = global_ns();
+  while (true) {
+    if (threadIdx.x == 0) {
+      int got;
+      while (true) {
+        const int pub = ld_volatile_i32(&Q.control[ASCHED_CTRL_PUBLISHED]);
+        const int cl = ld_volatile_i32(&Q.control[ASCHED_CTRL_CLAIMED]);
+        if (cl < pub) {
+          if (atomicCAS(&Q.control[ASCHED_CTRL_CLAIMED], cl, cl + 1) == cl) {
+            got = cl;
+            break;
+          }
+          continue;
+        }
+        if (ld_volatile_i32(&Q.control[ASCHED_CTRL_STOP])) {
+          got = -1;
+          break;
+        }
+        if (static_cast<int64_t>(global_ns() - idle_since) > Q.idle_ns) {
+          atomicAdd(&Q.control[ASCHED_CTRL_IDLE_EXITS], 1);
+          got = -1;
+          break;
+        }
+        __nanosleep(1000);
+      }
+      s_ticket = got;
+    }
+    __syncthreads();
+    const int t = s_ticket;
+    __syncthreads();
+    if (t < 0) break;
+    const int slot = ld_volatile_i32(&Q.ring[t % Q.ring_len]);
+    const int32_t* in = Q.slot_data + static_cast<int64_t>(slot) * Q.slot_words;
+    int32_t* out = Q.slot_out + static_cast<int64_t>(slot) * Q.out_words;
+    const int L = gin(in), V = gin(in + 1), M = gin(in + 2);
+    KParams P = Q.run;
+    P.L = L;
+    P.V = V;
+    P.M = M;
+    P.cap = gin(in + 3);
+    P.horizon = gin(in + 4);
+    const int flags = gin(in + 5);
+    const int32_t* vb = in + ASCHED_SLOT_HEADER + Q.nt * Q.Lc * Q.Lc;
+    P.travel = in + ASCHED_SLOT_HEADER;
+    P.veh_base = vb;
+    P.veh_type = vb + Q.Vc;
+    P.pickup = vb + 2 * Q.Vc;
+    P.delivery = P.pickup + Q.Mc;
+    P.heli_only = (flags & 1) ? P.delivery + Q.Mc : nullptr;
+    P.deadline = (flags & 2) ? P.delivery + 2 * Q.Mc : nullptr;
+    P.out_off = out;
+    P.out_route = out + Q.Vc + 1;
+    P.out_flight = P.out_route + Q.Mc;
+    P.out_over = P.out_flight + Q.Vc;
+    P.info = P.out_over + Q.Vc;
+    const bool sizes_ok = L >= 1 && L <= Q.Lc && V >= 1 && V <= Q.Vc && M >= 0 && M <= Q.Mc &&
+                          (DL == ((flags & 2) != 0));
+    if (sizes_ok) {
+      const Layout small = make_layout(M, V, L, Q.nt, false);
+      if (!Q.compact && small.total <= Q.smem_words) {
+        solve_one<PEN, DL, false, false>(P, small, 1, 0);
+      } else {
+        const Layout big = make_layout(M, V, L, Q.nt, true);
+        if (big.total <= Q.smem_words) {
+          solve_one<PEN, DL, false, true>(P, big, 1, 0);
+        } else if (threadIdx.x == 0) {
+          P.info[ASCHED_INFO_STATUS] = ASCHED_E_TOO_LARGE;
+        }
+      }
+    } else if (threadIdx.x == 0) {
+      P.info[ASCHED_INFO_STATUS] = ASCHED_E_INVALID;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence_system();
+      *reinterpret_cast<volatile int32_t*>(&Q.done[slot]) = gin(in + 6);
+      atomicAdd(&Q.control[ASCHED_CTRL_SERVED], 1);
+    }
+    idle_since = global_ns();
   }
 }
 
@@ -1455,6 +1575,82 @@ int launch_batch(const asched_batch* bt, const asched_params* p, const asched_ba
   return ASCHED_OK;
 }
 
+template <bool PEN, bool DL>
+void* serve_kernel_ptr() {
+  return reinterpret_cast<void*>(&serve_kernel<PEN, DL>);
+}
+
+int launch_serve(const asched_server* sv, const asched_params* p, int64_t idle_ns, int32_t max_ctas, void* stream) {
+  if (!sv || !p) return ASCHED_E_INVALID;
+  if (sv->n_slots < 1 || sv->ring_len < sv->n_slots || sv->max_loc < 1 || sv->max_vehicles < 1 ||
+      sv->max_missions < 0 || sv->n_types < 1 || sv->n_types > 2 || idle_ns <= 0)
+    return ASCHED_E_INVALID;
+  if (!sv->slot_data || !sv->slot_out || !sv->ring || !sv->control || !sv->done) return ASCHED_E_INVALID;
+  if (p->cluster_size > 1) return ASCHED_E_INVALID;
+  asched_instance cap = {};
+  cap.n_loc = sv->max_loc;
+  cap.n_types = sv->n_types;
+  cap.n_vehicles = sv->max_vehicles;
+  cap.n_missions = sv->max_missions;
+  int rc = check_sizes(&cap, p);
+  if (rc != ASCHED_OK) return rc;
+  const int limit = max_smem_optin();
+  if (limit < 0) return ASCHED_E_CUDA;
+  Layout lay;  // the largest request the slots can hold sizes the launch
+  rc = choose_layout(sv->max_missions, sv->max_vehicles, sv->max_loc, sv->n_types, p, limit, &lay);
+  if (rc != ASCHED_OK) return rc;
+  const int64_t bytes = static_cast<int64_t>(lay.total) * 4;
+  const bool pen = p->cap_mode == ASCHED_PENALTY;
+  const bool dl = sv->has_deadlines != 0;
+  void* fn = pen ? (dl ? serve_kernel_ptr<true, true>() : serve_kernel_ptr<true, false>())
+                 : (dl ? serve_kernel_ptr<false, true>() : serve_kernel_ptr<false, false>());
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)) !=
+      cudaSuccess)
+    return ASCHED_E_CUDA;
+  const int threads = p->block_threads ? p->block_threads : kMaxThreads;
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, static_cast<size_t>(bytes)) !=
+          cudaSuccess) {
+    (void)cudaGetLastError();
+    return ASCHED_E_CUDA;
+  }
+  if (per_sm < 1) return ASCHED_E_TOO_LARGE;
+  int grid = sms * per_sm;
+  if (max_ctas > 0 && max_ctas < grid) grid = max_ctas;
+  SParams q = {};
+  q.run.nt = sv->n_types;
+  q.run.tenure = p->tenure;
+  q.run.iterations = p->iterations;
+  q.run.lambda = pen ? p->lambda : 0;
+  q.run.cluster = 1;
+  q.run.timeout_ns = p->timeout_ns > 0 ? p->timeout_ns : kDefaultTimeoutNs;
+  q.n_slots = sv->n_slots;
+  q.ring_len = sv->ring_len;
+  q.Lc = sv->max_loc;
+  q.Vc = sv->max_vehicles;
+  q.Mc = sv->max_missions;
+  q.nt = sv->n_types;
+  q.slot_words = serve_slot_words(q.Lc, q.Vc, q.Mc, q.nt);
+  q.out_words = serve_out_words(q.Vc, q.Mc);
+  q.smem_words = lay.total;
+  q.compact = (p->flags & ASCHED_COMPACT_LAYOUT) ? 1 : 0;
+  q.idle_ns = idle_ns;
+  q.slot_data = sv->slot_data;
+  q.slot_out = sv->slot_out;
+  q.ring = sv->ring;
+  q.control = sv->control;
+  q.done = sv->done;
+  void* args[] = {&q};
+  if (cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, static_cast<size_t>(bytes),
+                       static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return ASCHED_E_CUDA;
+  }
+  return ASCHED_OK;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ fixed scratch ---
@@ -1582,6 +1778,21 @@ int asched_solve_batch_static(const asched_batch* batch, const asched_params* pa
   const int rc = static_scratch(&scratch);
   if (rc != ASCHED_OK) return rc;
   return launch_batch(batch, params, out, scratch, sizeof(g_batch_scratch), stream);
+}
+
+int asched_server_sizes(int32_t max_loc, int32_t max_vehicles, int32_t max_missions, int32_t n_types,
+                        int32_t* slot_words, int32_t* out_words) {
+  if (!slot_words || !out_words || max_loc < 1 || max_vehicles < 1 || max_missions < 0 || n_types < 1 ||
+      n_types > 2)
+    return ASCHED_E_INVALID;
+  *slot_words = serve_slot_words(max_loc, max_vehicles, max_missions, n_types);
+  *out_words = serve_out_words(max_vehicles, max_missions);
+  return ASCHED_OK;
+}
+
+int asched_serve(const asched_server* server, const asched_params* params, int64_t idle_timeout_ns,
+                 int32_t max_ctas, void* stream) {
+  return launch_serve(server, params, idle_timeout_ns, max_ctas, stream);
 }
 
 int asched_eval_neighbourhood(const asched_instance* inst, const asched_params* params,

@@ -295,3 +295,25 @@ def random_instance(seed: int, *, n_loc: int, n_vehicles: int, n_missions: int,
                     pickup=p.astype(np.int32), delivery=d.astype(np.int32), heli_only=heli,
                     deadline=dl, duty_cap=int(duty_cap), horizon=int(horizon),
                     name=name or f"random-s{seed}")
+
+
+SERVING_PARAMS = Params(tenure=10, iterations=1000, cap_mode=PENALTY, lam=1000)
+
+
+def serving_request(seed: int) -> Instance:
+    """One re-planning request: M = clip(round(lognormal(ln 60, 0.5)), 10, 400) missions,
+    V = ceil(M / 5) vehicles, paper-shaped geography (12 bases, 60 clustered facilities
+    in a 1500 km box), 12 h cap. Drawn from its own seed."""
+    rng = np.random.default_rng(seed)
+    m, v = serving_size(rng)
+    return make_instance(seed, n_bases=12, n_vehicles=v, n_facilities=60, n_missions=m,
+                         box_km=1500.0, geography="clustered", duty_cap=720,
+                         name=f"request-{seed}")
+
+
+def poisson_arrivals(seed: int, rate_per_s: float, duration_s: float) -> np.ndarray:
+    """Arrival times (seconds) of a Poisson stream: exponential gaps of mean 1 / rate."""
+    rng = np.random.default_rng(seed)
+    n = int(rate_per_s * duration_s * 1.2) + 16
+    t = np.cumsum(rng.exponential(1.0 / rate_per_s, size=n))
+    return t[t < duration_s]

@@ -1,0 +1,85 @@
+"""The request server (asched_serve + serve.Server): every request's result equals the
+result of solving it alone, however requests overlap on the device (needs a GB300)."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2002_11710_gb300 import api, gen, serve
+from paper_2002_11710_gb300._lib import CTRL_IDLE_EXITS
+
+pytestmark = pytest.mark.gpu
+
+
+def _alone(inst, params):
+    dp = api.DeviceProblem(inst)
+    out = api.solve(dp, params)
+    torch.cuda.synchronize()
+    return {"route_off": out.route_off.cpu().numpy()[: dp.V + 1], "route": out.route.cpu().numpy()[: dp.M],
+            "flight": out.flight.cpu().numpy()[: dp.V], "overflow": out.overflow.cpu().numpy()[: dp.V],
+            "info": out.info.cpu().numpy()}
+
+
+def _compare(got, want, V, M):
+    assert got["info"][api.INFO_STATUS] == want["info"][api.INFO_STATUS]
+    if want["info"][api.INFO_STATUS] != 0:
+        return False
+    for k in (api.INFO_Z_BEST, api.INFO_BEST_IT, api.INFO_Z_INIT, api.INFO_Z_FINAL, api.INFO_ITERS):
+        assert got["info"][k] == want["info"][k], k
+    np.testing.assert_array_equal(got["route_off"][: V + 1], want["route_off"])
+    np.testing.assert_array_equal(got["route"][:M], want["route"])
+    np.testing.assert_array_equal(got["flight"][:V], want["flight"])
+    np.testing.assert_array_equal(got["overflow"][:V], want["overflow"])
+    return True
+
+
+def test_served_results_equal_solving_alone_with_few_slots():
+    reqs = [gen.random_instance(700 + k, n_loc=6 + k % 11, n_vehicles=1 + k % 8, n_missions=(11 * k) % 70,
+                                n_types=2, heli_only_frac=0.2 if k % 3 else 0.0, duty_cap=1500,
+                                max_minutes=120) for k in range(36)]
+    params = api.make_params(5, 120, gen.PENALTY, 1000)
+    srv = serve.Server(max_loc=16, max_vehicles=8, max_missions=70, n_types=2, n_slots=5)
+    got = {}
+    srv.start(params, idle_timeout_s=30.0, max_ctas=8)
+    try:
+        arrivals = np.cumsum(np.random.default_rng(1).exponential(0.0004, size=len(reqs)))
+        lat, wall = serve.run_stream(srv, reqs, arrivals, on_done=lambda i, s: got.__setitem__(i, srv.result(s)))
+    finally:
+        srv.stop()
+    assert sorted(got) == list(range(len(reqs)))
+    assert srv.served() == len(reqs)
+    solved = sum(_compare(got[i], _alone(inst, params), inst.n_vehicles, inst.n_missions)
+                 for i, inst in enumerate(reqs))
+    assert solved >= 0.7 * len(reqs)
+
+
+def test_serving_workload_stream_sample():
+    """A short stream shaped like the serving workload (Poisson arrivals, lognormal sizes):
+    every request is served, and a sample equals solving it alone."""
+    arrivals = gen.poisson_arrivals(5, 2000.0, 0.1)
+    reqs = [gen.serving_request(10_000 + k) for k in range(len(arrivals))]
+    params = api.params_from(gen.SERVING_PARAMS)
+    srv = serve.Server(max_loc=72, max_vehicles=80, max_missions=400, n_slots=256)
+    got = {}
+    keep = set(range(0, len(reqs), 9))
+    srv.start(params, idle_timeout_s=30.0)
+    try:
+        lat, wall = serve.run_stream(srv, reqs, arrivals,
+                                     on_done=lambda i, s: got.__setitem__(i, srv.result(s)) if i in keep else None)
+    finally:
+        srv.stop()
+    assert srv.served() == len(reqs)
+    assert (lat > 0).all()
+    for i in sorted(keep):
+        assert _compare(got[i], _alone(reqs[i], params), reqs[i].n_vehicles, reqs[i].n_missions)
+
+
+def test_server_launch_ends_by_itself_when_idle():
+    srv = serve.Server(max_loc=8, max_vehicles=4, max_missions=10, n_slots=4)
+    t0 = time.perf_counter()
+    srv.start(api.make_params(3, 10, gen.PENALTY, 1000), idle_timeout_s=0.2, max_ctas=3)
+    srv.serve_stream.synchronize()
+    assert time.perf_counter() - t0 < 10.0
+    torch.cuda.synchronize()
+    assert int(srv.control[CTRL_IDLE_EXITS].item()) == 3
