@@ -390,3 +390,20 @@ def solve_batch_static(bp: BatchProblem, params: _lib.Params, out: Optional[Batc
                                                ctypes.byref(res), ctypes.c_void_p(s.cuda_stream))
     _lib.check(rc, "asched_solve_batch_static")
     return out
+
+
+def capture_batch(bp: BatchProblem, params: _lib.Params, out: Optional[BatchOutput] = None):
+    """Capture one asched_solve_batch (its ordering kernel and persistent launch) into a
+    CUDA graph. Returns (graph, out); graph.replay() reruns the whole batch into `out`.
+    The batch's inputs may be rewritten in place between replays (same sizes)."""
+    if out is None:
+        out = bp.alloc_output()
+    s = torch.cuda.Stream(device=bp.device)
+    s.wait_stream(torch.cuda.current_stream(bp.device))
+    with torch.cuda.stream(s):
+        solve_batch(bp, params, out=out, stream=s)  # warm-up outside the capture
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        solve_batch(bp, params, out=out, stream=s)
+    return g, out

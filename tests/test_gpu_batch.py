@@ -140,3 +140,19 @@ def test_batch_independent_of_block_size_and_autotuner_picks_a_candidate():
     best, times = api.autotune_batch(bp, api.make_params(4, 30, PENALTY, 1000), candidates=(256, 128),
                                      probe_iterations=10, repeats=1)
     assert best in (256, 128) and set(times) == {256, 128}
+
+
+def test_batch_replayed_from_a_cuda_graph_matches_direct_calls():
+    insts = _mixed_instances()
+    params = api.make_params(5, 50, PENALTY, 1000)
+    bp = api.BatchProblem(insts)
+    direct = api.solve_batch(bp, params)
+    torch.cuda.synchronize()
+    g, out = api.capture_batch(bp, params)
+    for _ in range(3):
+        out.info.zero_()
+        out.route.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        for b in range(len(insts)):
+            _same(bp.unpack(out, b), bp.unpack(direct, b))
