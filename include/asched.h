@@ -116,13 +116,19 @@ typedef struct {
  *                       on it.
  *   block_threads       0 = automatic, else a multiple of 32 in [64, 512].
  *   timeout_ns          bound on every wait between CTAs; 0 = 1 s.
- *   flags               0, or ASCHED_COMPACT_LAYOUT.
+ *   flags               0, or a combination of ASCHED_COMPACT_LAYOUT and
+ *                       ASCHED_TEST_WITHHOLD_KEY.
  * Shared-memory layout: instances whose location x mission gather tables fit in one
  * CTA's shared memory use them; larger ones (or all, with ASCHED_COMPACT_LAYOUT) keep
  * the travel matrix itself as int16 instead, which needs every travel time <= 32,767
  * (else ASCHED_E_TOO_LARGE on the device) and iterations + tenure <= 32,767 (else
  * ASCHED_E_TOO_LARGE from the call). Results do not depend on the layout. */
 #define ASCHED_COMPACT_LAYOUT 1u
+/* Failure-path test hook for asched_solve with cluster_size >= 2: the last CTA of the
+ * cluster does not publish its key in the first iteration, so every CTA's bounded wait
+ * runs out after timeout_ns and the call reports ASCHED_E_TIMEOUT (nothing faults or
+ * hangs). No effect with one CTA. */
+#define ASCHED_TEST_WITHHOLD_KEY 2u
 typedef struct {
   int32_t tenure;
   int32_t iterations;

@@ -23,7 +23,8 @@ STATIC_BATCH_MAX = 16384  # ASCHED_STATIC_BATCH_MAX
 
 HARD = 0
 PENALTY = 1
-COMPACT_LAYOUT = 1  # asched_params.flags bit
+COMPACT_LAYOUT = 1  # asched_params.flags bits
+TEST_WITHHOLD_KEY = 2
 
 FLAG_FEASIBLE, FLAG_TABU, FLAG_ASPIRATION, FLAG_ADMISSIBLE = 1, 2, 4, 8
 SWAP_BIT = 0x80000000

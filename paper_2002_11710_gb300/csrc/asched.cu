@@ -132,6 +132,7 @@ struct KParams {
   const int32_t* deadline;
   int32_t L, nt, V, M, cap, horizon;
   int32_t tenure, iterations, lambda, cluster;
+  int32_t test_withhold;  // the last CTA does not publish its first key (tests the timeout)
   int64_t timeout_ns;
   Layout lay;
   const int32_t* init_off;
@@ -884,7 +885,8 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
         // iteration's tag (bounded by the timeout).
         const int sb = it & 1;
         const uint64_t tag = iter_tag(it);
-        if (warp == 0 && lane < C) {
+        const bool withhold = P.test_withhold && it == 0 && rank == C - 1;  // test hook
+        if (warp == 0 && lane < C && !withhold) {
           const uint32_t slot_addr = smem_u32(&sm.slots()[sb * kMaxCluster + rank]);
           st_peer_u64(mapa_rank(slot_addr, lane), (gk & ~kTagMask) | tag);
         }
@@ -909,9 +911,22 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
           if ((gk >> 32) == 0xFFFFFFFFull) gk = kNoKey;  // real deltas never reach 2^31 - 1
         }
       }
+      // A chosen move must name nodes of this instance; anything else ends the solve
+      // (gk is the same in every thread of the cluster, so this decision is too).
+      bool bad_key = false;
+      if (!timed_out && gk != kNoKey) {
+        const uint32_t id = static_cast<uint32_t>(gk);
+        if (id & kSwapBit) {
+          const uint32_t a = (id >> kIdShift) & kIdMask, b = id & kIdMask;
+          bad_key = !(a < b && b < static_cast<uint32_t>(M));
+        } else {
+          const uint32_t m = id >> kIdShift, y = id & kIdMask;
+          bad_key = !(m < static_cast<uint32_t>(M) && y < static_cast<uint32_t>(N) && y != m);
+        }
+      }
       if (DEBUG) {
         if (rank == 0 && tid == 0 && !timed_out) *P.dbg_key = gk;
-      } else if (!timed_out && gk != kNoKey) {
+      } else if (!timed_out && !bad_key && gk != kNoKey) {
         // ---- apply the chosen move: every thread decodes it from the current buffer,
         // then rewrites the records of its nodes into the other buffer.
         const State S2 = sm.st(cur ^ 1);
@@ -1039,8 +1054,8 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
         if (P.traj_move) P.traj_move[it] = gk == kNoKey ? kNullMove : static_cast<uint32_t>(gk);
         if (P.traj_z) P.traj_z[it] = Z;
       }
-      if (__syncthreads_or(timed_out)) {
-        status = ASCHED_E_TIMEOUT;
+      if (__syncthreads_or(timed_out || bad_key)) {
+        status = bad_key ? ASCHED_E_INVALID : ASCHED_E_TIMEOUT;
         break;
       }
       if (!DEBUG && gk != kNoKey) cur ^= 1;
@@ -1373,7 +1388,8 @@ int check_sizes(const asched_instance* inst, const asched_params* p) {
     return ASCHED_E_INVALID;
   if (p->block_threads != 0 && (p->block_threads < 64 || p->block_threads > kMaxThreads || p->block_threads % 32))
     return ASCHED_E_INVALID;
-  if (p->timeout_ns < 0 || (p->flags & ~ASCHED_COMPACT_LAYOUT) != 0) return ASCHED_E_INVALID;
+  if (p->timeout_ns < 0 || (p->flags & ~(ASCHED_COMPACT_LAYOUT | ASCHED_TEST_WITHHOLD_KEY)) != 0)
+    return ASCHED_E_INVALID;
   return ASCHED_OK;
 }
 
@@ -1443,6 +1459,7 @@ int launch(const asched_instance* inst, const asched_params* p, bool debug, KPar
   kp.lambda = pen ? p->lambda : 0;
   kp.cluster = plan.cluster_size;
   kp.timeout_ns = p->timeout_ns > 0 ? p->timeout_ns : kDefaultTimeoutNs;
+  kp.test_withhold = (p->flags & ASCHED_TEST_WITHHOLD_KEY) ? 1 : 0;
   kp.lay = lay;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.smem_bytes) != cudaSuccess)
     return ASCHED_E_CUDA;

@@ -329,3 +329,19 @@ def test_host_side_errors():
     out = api.solve(api.DeviceProblem(wide), api.make_params(3, 5, PENALTY, 1, compact=True))
     torch.cuda.synchronize()
     assert int(out.info[api.INFO_STATUS]) == api.E_TOO_LARGE
+
+
+@pytest.mark.parametrize("cluster", [2, 16])
+def test_bounded_wait_reports_timeout_and_context_stays_usable(cluster):
+    """A CTA that never publishes its key (test hook) makes every peer's bounded wait run
+    out: the call ends with ASCHED_E_TIMEOUT, and the next solve in the same context is
+    correct."""
+    inst = gen.random_instance(95, n_loc=10, n_vehicles=4, n_missions=30, duty_cap=2000)
+    dp = api.DeviceProblem(inst)
+    params = api.make_params(4, 50, PENALTY, 1000, cluster_size=cluster, timeout_ns=50_000_000)
+    params.flags |= api._lib.TEST_WITHHOLD_KEY
+    out = api.solve(dp, params)
+    torch.cuda.synchronize()
+    assert int(out.info[api.INFO_STATUS]) == api.E_TIMEOUT
+    assert int(out.info[api.INFO_ITERS]) == 0
+    _check_solve_vs_oracle(inst, PENALTY, 4, 50, cluster_size=cluster)
