@@ -1,4 +1,4 @@
-"""Plain CPU oracle for the Tabu search of arXiv 2002.11710 (Algorithms 1 and 3).
+"""Plain CPU oracle for the search methods of arXiv 2002.11710 (Algorithms 1, 2 and 3).
 
 TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the CPU baseline leg of
 ``bench.py`` are the only callers. The product path (the CUDA library and its
@@ -84,6 +84,12 @@ def lib():
             L.orc_tabu_search.restype = ctypes.c_int32
             L.orc_tabu_search.argtypes = [P, ctypes.c_int32, ctypes.c_int32, P, P, P, P, P, P,
                                           P, P]
+            L.orc_neighbourhood_search.restype = ctypes.c_int32
+            L.orc_neighbourhood_search.argtypes = [P, ctypes.c_int32, P, P, P, P, P, P, P, P,
+                                                   ctypes.c_int64]
+            L.orc_tabu_sweep.restype = ctypes.c_int32
+            L.orc_tabu_sweep.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P,
+                                         P, P, P, P, P, P, ctypes.c_int64]
             _lib = L
     return _lib
 
@@ -192,3 +198,38 @@ def tabu_search(pb: Problem, tenure: int, iterations: int, init=None):
     return {"status": int(rc), "route_off": off, "route": route[:pb.M], "z_best": int(zb.value),
             "best_it": int(bi.value), "traj_move": traj_move[:iterations],
             "traj_z": traj_z[:iterations]}
+
+
+def _sweep(pb: Problem, fn, args, init, trace_cap):
+    off = np.zeros(pb.V + 1, dtype=np.int32)
+    route = np.zeros(max(pb.M, 1), dtype=np.int32)
+    moves = np.zeros(max(trace_cap, 1), dtype=np.uint32)
+    zs = np.zeros(max(trace_cap, 1), dtype=np.int64)
+    zo = np.zeros(3, dtype=np.int64)
+    counts = np.zeros(4, dtype=np.int32)
+    if init is not None:
+        ioff = np.ascontiguousarray(init[0], dtype=np.int32)
+        iroute = np.ascontiguousarray(init[1], dtype=np.int32)
+        ip = (_ptr(ioff), _ptr(iroute))
+    else:
+        ip = (None, None)
+    rc = fn(pb.ref, *args, ip[0], ip[1], _ptr(off), _ptr(route), _ptr(zo), _ptr(counts),
+            _ptr(moves), _ptr(zs), int(trace_cap))
+    n = min(int(counts[2]), trace_cap)
+    return {"status": int(rc), "route_off": off, "route": route[:pb.M], "z_best": int(zo[0]),
+            "z_init": int(zo[1]), "z_final": int(zo[2]), "sweeps": int(counts[0]),
+            "n_moves": int(counts[1]), "steps": int(counts[2]), "best_step": int(counts[3]),
+            "trace_move": moves[:n], "trace_z": zs[:n]}
+
+
+def neighbourhood_search(pb: Problem, max_sweeps: int, init=None, trace_cap: int = 1 << 16):
+    """Algorithm 2 (readings S1-S3, S5 in the C file). One trace entry per mission step."""
+    return _sweep(pb, lib().orc_neighbourhood_search, (int(max_sweeps),), init, trace_cap)
+
+
+def tabu_sweep(pb: Problem, tenure: int, max_sweeps: int, accept_worse: bool = False, init=None,
+               trace_cap: int = 1 << 16):
+    """Algorithm 3 as printed: per-mission sweep with a tabu list (readings S1, S2, S4 or,
+    with accept_worse, S4b; S5)."""
+    return _sweep(pb, lib().orc_tabu_sweep, (int(tenure), int(max_sweeps), int(bool(accept_worse))),
+                  init, trace_cap)

@@ -530,3 +530,160 @@ int32_t orc_tabu_search(const orc_instance *in, int32_t tenure, int32_t iteratio
   free(ids);
   return rc;
 }
+
+/* ------------------------------------------------------------------------------------
+ * Algorithm 2 (Neighbourhood Search) and Algorithm 3 as printed (a per-mission sweep
+ * with a tabu list), under these readings:
+ *   S1  A sweep takes vehicles i = 0..V-1 in order; the missions j tried for i are i's
+ *       route as it stands when i's turn starts, in route order. (During i's turn
+ *       missions only leave i, each at most once, so this is well defined.) Trying one
+ *       mission is one step; steps are counted from 0 over the whole search.
+ *   S2  Candidates for j: every other vehicle k (index order) whose type may fly j
+ *       (con9), and on k every insertion point q = 0..n_k in order (q = n_k appends).
+ *       The first insertion point whose schedule is infeasible (duty cap in HARD mode,
+ *       deadlines) ends the scan of k: the later points of k are not tried (the
+ *       listings' "continue to the next base" inside the loop over positions).
+ *   S3  Algorithm 2 applies the candidate with the least (delta, k, q) when its delta
+ *       is negative (the best position starts as j's current one); sweeps repeat while
+ *       a sweep applied a move, at most max_sweeps.
+ *   S4  Algorithm 3: the tabu list holds pairs (mission, vehicle). A pair (j, k) whose
+ *       counter has not run out takes base k out of j's scan (the listing's "continue
+ *       to the next k"); there is no aspiration. As in S3 the least (delta, k, q) of the
+ *       other candidates is applied only when delta < 0 (the text adds an entry to the
+ *       list only for a move that improves); applying it at step s from vehicle i makes
+ *       (j, i) tabu through step s + tenure. Sweeps repeat while a sweep applied a move,
+ *       at most max_sweeps.
+ *   S4b The listing alone also reads as applying the least admissible candidate even
+ *       when delta >= 0 (CurrentMin starting empty). Option accept_worse takes that
+ *       reading; sweeps then repeat while a sweep lowered the best objective.
+ *   S5  The result is the best schedule met (the first to reach the least objective).
+ *   Trace: one entry per step, the relocation id (j << 13) | y of the applied move (y
+ *   the node j now precedes: a mission, or M + k at the end of route k) or 0xFFFFFFFF
+ *   when nothing was applied, and the objective after the step.
+ * ------------------------------------------------------------------------------------ */
+
+static int sweep_search(const orc_instance *in, int use_tabu, int accept_worse, int32_t tenure,
+                        int32_t max_sweeps,
+                        const int32_t *init_off, const int32_t *init_route, int32_t *best_off,
+                        int32_t *best_route, int64_t *z_best_out, int32_t *counts_out,
+                        uint32_t *trace_move, int64_t *trace_z, int64_t trace_cap) {
+  int rc = check_instance(in);
+  if (rc != ORC_OK) return rc;
+  int M = in->n_missions, V = in->n_vehicles;
+  int32_t *off = (int32_t *)malloc(sizeof(int32_t) * (size_t)(V + 1));
+  int32_t *route = (int32_t *)malloc(sizeof(int32_t) * (size_t)(M > 0 ? M : 1));
+  int64_t *tabu = (int64_t *)malloc(sizeof(int64_t) * (size_t)(M > 0 ? M : 1) * (size_t)V);
+  int32_t *snap = (int32_t *)malloc(sizeof(int32_t) * (size_t)(M > 0 ? M : 1));
+  sched s, t, best_t;
+  if (!off || !route || !tabu || !snap || sched_alloc(&s, V, M) != ORC_OK ||
+      sched_alloc(&t, V, M) != ORC_OK || sched_alloc(&best_t, V, M) != ORC_OK)
+    return ORC_E_NOMEM;
+  if (init_off) {
+    memcpy(off, init_off, sizeof(int32_t) * (size_t)(V + 1));
+    memcpy(route, init_route, sizeof(int32_t) * (size_t)M);
+    if (sched_from_csr(&s, off, route) != ORC_OK || !orc_feasible(in, off, route))
+      rc = ORC_E_INFEASIBLE_INIT;
+  } else {
+    rc = orc_greedy_init(in, off, route);
+  }
+  int64_t sweeps = 0, n_moves = 0, step = 0, best_step = -1;
+  int64_t z = 0, z_best = 0, z_init = 0;
+  if (rc == ORC_OK) {
+    sched_from_csr(&s, off, route);
+    for (int64_t x = 0; x < (int64_t)(M > 0 ? M : 1) * V; x++) tabu[x] = -1;
+    z = sched_cost(in, &s, NULL, NULL);
+    z_best = z_init = z;
+    sched_copy(&best_t, &s);
+    int go_on = 1;
+    while (go_on && sweeps < max_sweeps) {
+      int applied = 0;
+      int64_t z_best_before = z_best;
+      for (int i = 0; i < V; i++) {
+        int ni = s.len[i];
+        memcpy(snap, s.seq + (int64_t)i * M, sizeof(int32_t) * (size_t)ni);
+        for (int jj = 0; jj < ni; jj++) {
+          int j = snap[jj], vj, kj;
+          uint32_t rec = ORC_NULL_MOVE;
+          if (locate(&s, j, &vj, &kj) && vj == i) {
+            int best_k = -1, best_q = -1;
+            int64_t best_d = 0;
+            for (int k = 0; k < V; k++) {
+              if (k == i) continue;
+              if (in->heli_only && in->heli_only[j] && in->veh_type[k] != 0) continue;
+              if (use_tabu && tabu[(int64_t)j * V + k] >= step) continue; /* S4 */
+              for (int q = 0; q <= s.len[k]; q++) {
+                sched_copy(&t, &s);
+                remove_at(&t, i, kj);
+                insert_at(&t, k, q, j);
+                if (!sched_feasible(in, &t)) break; /* S2 */
+                int64_t d = sched_cost(in, &t, NULL, NULL) - z;
+                if (best_k < 0 || d < best_d) {
+                  best_k = k;
+                  best_q = q;
+                  best_d = d;
+                }
+              }
+            }
+            if (best_k >= 0 && (best_d < 0 || accept_worse)) {
+              int y = best_q < s.len[best_k] ? s.seq[(int64_t)best_k * M + best_q] : M + best_k;
+              remove_at(&s, i, kj);
+              insert_at(&s, best_k, best_q, j);
+              z = sched_cost(in, &s, NULL, NULL);
+              if (use_tabu) tabu[(int64_t)j * V + i] = step + tenure;
+              rec = ((uint32_t)j << 13) | (uint32_t)y;
+              n_moves++;
+              applied = 1;
+              if (z < z_best) {
+                z_best = z;
+                best_step = step;
+                sched_copy(&best_t, &s);
+              }
+            }
+          }
+          if (step < trace_cap) {
+            if (trace_move) trace_move[step] = rec;
+            if (trace_z) trace_z[step] = z;
+          }
+          step++;
+        }
+      }
+      sweeps++;
+      go_on = accept_worse ? (z_best < z_best_before) : applied;
+    }
+    sched_to_csr(&best_t, best_off, best_route);
+  }
+  *z_best_out = z_best;
+  counts_out[0] = (int32_t)sweeps;
+  counts_out[1] = (int32_t)n_moves;
+  counts_out[2] = (int32_t)step;
+  counts_out[3] = (int32_t)best_step;
+  z_best_out[1] = z_init;
+  z_best_out[2] = z;
+  free(off);
+  free(route);
+  free(tabu);
+  free(snap);
+  sched_free(&s);
+  sched_free(&t);
+  sched_free(&best_t);
+  return rc;
+}
+
+/* Algorithm 2 (readings S1-S3, S5). z_out[3] = {best, initial, final} objectives;
+ * counts_out[4] = {sweeps, moves applied, steps, step of the best (-1: initial)}. */
+int32_t orc_neighbourhood_search(const orc_instance *in, int32_t max_sweeps, const int32_t *init_off,
+                                 const int32_t *init_route, int32_t *best_off, int32_t *best_route,
+                                 int64_t *z_out, int32_t *counts_out, uint32_t *trace_move,
+                                 int64_t *trace_z, int64_t trace_cap) {
+  return sweep_search(in, 0, 0, 0, max_sweeps, init_off, init_route, best_off, best_route, z_out,
+                      counts_out, trace_move, trace_z, trace_cap);
+}
+
+/* Algorithm 3 as printed (readings S1, S2, S4 or S4b, S5); outputs as above. */
+int32_t orc_tabu_sweep(const orc_instance *in, int32_t tenure, int32_t max_sweeps, int32_t accept_worse,
+                       const int32_t *init_off,
+                       const int32_t *init_route, int32_t *best_off, int32_t *best_route, int64_t *z_out,
+                       int32_t *counts_out, uint32_t *trace_move, int64_t *trace_z, int64_t trace_cap) {
+  return sweep_search(in, 1, accept_worse != 0, tenure, max_sweeps, init_off, init_route, best_off, best_route, z_out,
+                      counts_out, trace_move, trace_z, trace_cap);
+}

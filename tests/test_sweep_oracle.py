@@ -1,0 +1,264 @@
+"""Pins of the oracle's Algorithm 2 / Algorithm 3 sweeps (readings S1-S5) against things
+other than the oracle itself (no GPU needed).
+
+* the hand-worked instance tests/golden/line_sweep.json;
+* every trace replayed on plain Python routes, its objectives recomputed with the
+  ILP's arc form (tests/ilp.py) and every schedule on the way checked against
+  con1-con11;
+* every step re-derived by brute force: the mission tried, its candidates built as
+  explicit schedules, the break rule, the least (delta, k, q), the tabu pairs;
+* closed properties: Neighbourhood Search ends in a local optimum of its own
+  candidate set and descends strictly; tenure 0 reduces Algorithm 3 to Algorithm 2;
+  a single vehicle has no candidate.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import ilp
+import oracle
+from paper_2002_11710_gb300 import gen
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+NULL = 0xFFFFFFFF
+
+
+def _line_sweep():
+    with open(os.path.join(GOLDEN, "line_sweep.json")) as f:
+        g = json.load(f)
+    gi = g["instance"]
+    x = gi["coordinates_minutes"]
+    n = len(x)
+    T = np.array([[abs(x[str(i)] - x[str(j)]) for j in range(n)] for i in range(n)], dtype=np.int32)
+    inst = gen.Instance(travel=T[None], veh_base=np.array(gi["veh_base"], dtype=np.int32),
+                        veh_type=np.array(gi["veh_type"], dtype=np.int32),
+                        pickup=np.array(gi["pickup"], dtype=np.int32),
+                        delivery=np.array(gi["delivery"], dtype=np.int32), heli_only=None,
+                        deadline=None, duty_cap=gi["duty_cap"], horizon=gi["horizon"],
+                        name="line_sweep")
+    return g, inst
+
+
+def test_golden_line_sweep():
+    g, inst = _line_sweep()
+    pb = oracle.Problem(inst, g["instance"]["cap_mode"], g["instance"]["lambda"])
+    rc, off, route = oracle.greedy_init(pb)
+    assert rc == 0
+    assert off.tolist() == g["greedy"]["route_off"] and route.tolist() == g["greedy"]["route"]
+    ns = oracle.neighbourhood_search(pb, 50)
+    e = g["neighbourhood_search"]
+    assert ns["status"] == 0 and ns["z_init"] == g["greedy"]["z"]
+    assert ns["trace_move"].tolist() == e["trace_move"]
+    assert ns["trace_z"].tolist() == e["trace_z"]
+    assert ns["route_off"].tolist() == e["route_off"] and ns["route"].tolist() == e["route"]
+    assert (ns["z_best"], ns["best_step"], ns["sweeps"], ns["n_moves"], ns["steps"]) == \
+        (e["z_best"], e["best_step"], e["sweeps"], e["moves"], e["steps"])
+    ts = oracle.tabu_sweep(pb, 2, 50)
+    assert ts["trace_move"].tolist() == g["tabu_sweep_tenure_2"]["trace_move"]
+    assert ts["z_best"] == g["tabu_sweep_tenure_2"]["z_best"]
+
+
+# (seed, n_loc, V, M, n_types, heli-only fraction, deadlines, duty cap)
+CASES = [
+    (11, 6, 2, 4, 1, 0.0, False, 400),
+    (12, 7, 3, 5, 2, 0.4, False, 500),
+    (13, 8, 3, 6, 2, 0.3, True, 900),
+    (14, 9, 4, 7, 2, 0.3, False, 350),
+    (15, 10, 4, 9, 2, 0.25, True, 1200),
+    (16, 12, 5, 11, 2, 0.2, False, 600),
+]
+
+
+def _inst(case):
+    seed, L, V, M, nt, heli, dl, cap = case
+    return gen.random_instance(seed, n_loc=L, n_vehicles=V, n_missions=M, n_types=nt,
+                               heli_only_frac=heli, deadlines=dl, deadline_lo=300,
+                               duty_cap=cap, max_minutes=200)
+
+
+def _variants():
+    # (name, runner, is_tabu, tenure, accept_worse)
+    return [("ns", lambda pb: oracle.neighbourhood_search(pb, 40), False, 0, False),
+            ("ts3", lambda pb: oracle.tabu_sweep(pb, 3, 40), True, 3, False),
+            ("ts3w", lambda pb: oracle.tabu_sweep(pb, 3, 12, accept_worse=True), True, 3, True),
+            ("ts9w", lambda pb: oracle.tabu_sweep(pb, 9, 12, accept_worse=True), True, 9, True)]
+
+
+def _routes_of(pb, off, route):
+    return [list(r) for r in ilp.csr_to_routes(off, route, pb.V)]
+
+
+def _where(routes, m):
+    for v, r in enumerate(routes):
+        if m in r:
+            return v, r.index(m)
+    raise AssertionError(m)
+
+
+def _compatible(inst, m, k):
+    return inst.heli_only is None or not int(inst.heli_only[m]) or int(inst.veh_type[k]) == 0
+
+
+def _rederive(inst, mode, lam, routes, is_tabu, tenure, accept_worse, max_sweeps):
+    """Algorithm 2/3 re-derived step by step on explicit schedules (readings S1-S5)."""
+    M, V = inst.n_missions, inst.n_vehicles
+    z = ilp.objective(inst, tuple(map(tuple, routes)), mode, lam)
+    z_best, best = z, [list(r) for r in routes]
+    tabu = {}
+    trace = []
+    sweeps = 0
+    go_on = True
+    while go_on and sweeps < max_sweeps:
+        applied = False
+        zb0 = z_best
+        for i in range(V):
+            for j in list(routes[i]):
+                rec = NULL
+                if j in routes[i]:
+                    kj = routes[i].index(j)
+                    cands = []
+                    for k in range(V):
+                        if k == i or not _compatible(inst, j, k):
+                            continue
+                        if is_tabu and tabu.get((j, k), -1) >= len(trace):
+                            continue
+                        for q in range(len(routes[k]) + 1):
+                            t = [list(r) for r in routes]
+                            del t[i][kj]
+                            t[k].insert(q, j)
+                            tt = tuple(map(tuple, t))
+                            if not ilp.feasible(inst, tt, mode):
+                                break
+                            cands.append((ilp.objective(inst, tt, mode, lam) - z, k, q))
+                    if cands:
+                        d, k, q = min(cands)
+                        if d < 0 or accept_worse:
+                            y = routes[k][q] if q < len(routes[k]) else M + k
+                            del routes[i][kj]
+                            routes[k].insert(q, j)
+                            z += d
+                            if is_tabu:
+                                tabu[(j, i)] = len(trace) + tenure
+                            rec = (j << 13) | y
+                            applied = True
+                            if z < z_best:
+                                z_best, best = z, [list(r) for r in routes]
+                trace.append((rec, z))
+        sweeps += 1
+        go_on = (z_best < zb0) if accept_worse else applied
+    return trace, z_best, best, sweeps
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("mode", [ilp.HARD, ilp.PENALTY])
+def test_sweeps_rederived_by_brute_force(case, mode):
+    inst = _inst(case)
+    pb = oracle.Problem(inst, mode, 1000)
+    rc, off, route = oracle.greedy_init(pb)
+    if rc != 0:
+        pytest.skip("greedy start infeasible for this case")
+    for name, run, is_tabu, tenure, aw in _variants():
+        r = run(pb)
+        assert r["status"] == 0, name
+        max_sweeps = 40 if not aw else 12
+        trace, zb, best, sweeps = _rederive(inst, mode, 1000, _routes_of(pb, off, route), is_tabu,
+                                            tenure, aw, max_sweeps)
+        assert r["trace_move"].tolist() == [t[0] for t in trace], name
+        assert r["trace_z"].tolist() == [t[1] for t in trace], name
+        assert r["z_best"] == zb and r["sweeps"] == sweeps, name
+        assert _routes_of(pb, r["route_off"], r["route"]) == best, name
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("mode", [ilp.HARD, ilp.PENALTY])
+def test_trace_replays_on_feasible_schedules(case, mode):
+    """Each applied move relocates one mission to another, compatible vehicle; each
+    schedule on the way satisfies con1-con11 and has the traced objective."""
+    inst = _inst(case)
+    pb = oracle.Problem(inst, mode, 1000)
+    rc, off, route = oracle.greedy_init(pb)
+    if rc != 0:
+        pytest.skip("greedy start infeasible for this case")
+    M = inst.n_missions
+    for name, run, is_tabu, tenure, aw in _variants():
+        r = run(pb)
+        routes = _routes_of(pb, off, route)
+        z = ilp.objective(inst, tuple(map(tuple, routes)), mode, 1000)
+        assert r["z_init"] == z
+        zs = [z]
+        left = {}
+        for s, (mv, zt) in enumerate(zip(r["trace_move"].tolist(), r["trace_z"].tolist())):
+            if mv != NULL:
+                j, y = mv >> 13, mv & 0x1FFF
+                vi, ki = _where(routes, j)
+                del routes[vi][ki]
+                if y < M:
+                    k, q = _where(routes, y)
+                else:
+                    k, q = y - M, len(routes[y - M])
+                assert k != vi and _compatible(inst, j, k)
+                if is_tabu:
+                    assert left.get((j, k), -1) < s, "move onto a tabu base"
+                    left[(j, vi)] = s + tenure
+                routes[k].insert(q, j)
+                tt = tuple(map(tuple, routes))
+                assert ilp.feasible(inst, tt, mode)
+                znew = ilp.objective(inst, tt, mode, 1000)
+                if not aw:
+                    assert znew < zs[-1], "Algorithm 2 / 3 apply improving moves only"
+                zs.append(znew)
+            assert zt == zs[-1]
+        assert r["z_final"] == zs[-1]
+        assert r["z_best"] == min(zs)
+        assert ilp.objective(inst, ilp.csr_to_routes(r["route_off"], r["route"], pb.V), mode,
+                             1000) == r["z_best"]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_neighbourhood_search_ends_in_a_local_optimum(case):
+    inst = _inst(case)
+    pb = oracle.Problem(inst, ilp.PENALTY, 1000)
+    r = oracle.neighbourhood_search(pb, 1000)
+    assert r["status"] == 0 and r["sweeps"] < 1000
+    routes = _routes_of(pb, r["route_off"], r["route"])
+    z = ilp.objective(inst, tuple(map(tuple, routes)), ilp.PENALTY, 1000)
+    for i, ri in enumerate(routes):
+        for kj, j in enumerate(ri):
+            for k in range(inst.n_vehicles):
+                if k == i or not _compatible(inst, j, k):
+                    continue
+                for q in range(len(routes[k]) + 1):
+                    t = [list(x) for x in routes]
+                    del t[i][kj]
+                    t[k].insert(q, j)
+                    tt = tuple(map(tuple, t))
+                    if not ilp.feasible(inst, tt, ilp.PENALTY):
+                        break
+                    assert ilp.objective(inst, tt, ilp.PENALTY, 1000) >= z
+
+
+def test_tenure_zero_is_neighbourhood_search():
+    for seed, m in [(0, 20), (2, 24), (8, 33)]:
+        pb = oracle.Problem(gen.paper_model(seed, m), ilp.PENALTY, 1000)
+        a = oracle.neighbourhood_search(pb, 100)
+        b = oracle.tabu_sweep(pb, 0, 100)
+        assert a["trace_move"].tolist() == b["trace_move"].tolist()
+        assert a["z_best"] == b["z_best"]
+
+
+def test_single_vehicle_has_no_candidate():
+    inst = gen.random_instance(21, n_loc=8, n_vehicles=1, n_missions=6, n_types=1, duty_cap=10000)
+    pb = oracle.Problem(inst, ilp.PENALTY, 1000)
+    for r in (oracle.neighbourhood_search(pb, 10), oracle.tabu_sweep(pb, 3, 10, accept_worse=True)):
+        assert r["n_moves"] == 0 and r["steps"] == 6
+        assert (r["trace_move"] == NULL).all()
+        assert r["z_best"] == r["z_init"] == r["z_final"]
+
+
+def test_sweep_reports_infeasible_start():
+    bad = gen.random_instance(401, n_loc=8, n_vehicles=2, n_missions=12, duty_cap=10)
+    pb = oracle.Problem(bad, ilp.HARD, 1000)
+    assert oracle.neighbourhood_search(pb, 5)["status"] == oracle.E_INFEASIBLE_INIT
+    assert oracle.tabu_sweep(pb, 3, 5)["status"] == oracle.E_INFEASIBLE_INIT
