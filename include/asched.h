@@ -365,6 +365,64 @@ int asched_serve(const asched_server* server, const asched_params* params, int64
 int asched_solve_batch_static(const asched_batch* batch, const asched_params* params,
                               const asched_batch_result* out, void* stream);
 
+/* ---------------------------------------------------------------- sweeps -----------
+ * The paper's own local searches in the per-mission sweep form it prints, on every
+ * instance of a batch (one CTA per instance):
+ *   ASCHED_SWEEP_NEIGHBOURHOOD  Algorithm 2 (Neighbourhood Search, Section 4.2);
+ *   ASCHED_SWEEP_TABU           Algorithm 3 as printed (Section 4.3).
+ * Each starts from the greedy schedule of Algorithm 1 and sweeps vehicles i = 0..V-1
+ * in order; for i, the missions j of i's route as it stands when i's turn starts, in
+ * route order (one step each, counted over the whole search), are relocated:
+ *   - candidates: every other vehicle k whose type may fly j (con9), at every insertion
+ *     point q = 0..n_k in order; the first q whose schedule breaks the duty cap (HARD)
+ *     or an arrive-by time ends the scan of k (the listings' "continue to the next
+ *     base" inside the position loop);
+ *   - Algorithm 3 also skips every k with (j, k) on the tabu list; applying a move of
+ *     j off vehicle i at step s puts (j, i) on the list through step s + tenure (no
+ *     aspiration);
+ *   - the least (delta, k, q) is applied when delta < 0; with ASCHED_SWEEP_ACCEPT_WORSE
+ *     (Algorithm 3 only) it is applied whatever its delta.
+ * Sweeps repeat while one applied a move (ACCEPT_WORSE: while one lowered the best
+ * objective), at most params->iterations sweeps. The result is the first schedule
+ * that reached the least objective. */
+#define ASCHED_SWEEP_NEIGHBOURHOOD 2
+#define ASCHED_SWEEP_TABU 3
+#define ASCHED_SWEEP_ACCEPT_WORSE 4u /* asched_params.flags bit for the sweeps */
+/* asched_params.flags bit for the sweeps: Algorithm 1's repair. When no vehicle can take
+ * the next mission and some mission is already placed, one Neighbourhood Search sweep
+ * (the rules above, on the partial schedule) runs and the mission is tried once more
+ * (Section 4.1 leaves a stuck placement to "mission swaps" of Algorithm 2 and a retry).
+ * Without it, or if the retry fails too, info[ASCHED_INFO_STATUS] is
+ * ASCHED_E_INFEASIBLE_INIT. */
+#define ASCHED_SWEEP_REPAIR 8u
+
+/* info[] of a sweep: ASCHED_INFO_STATUS, _Z_BEST, _Z_INIT, _Z_FINAL as above;
+ * ASCHED_INFO_BEST_IT = step that reached the best (-1: the greedy schedule);
+ * ASCHED_INFO_ITERS = sweeps run; and: */
+#define ASCHED_INFO_MOVES 6 /* moves applied */
+#define ASCHED_INFO_STEPS 7 /* mission steps taken */
+
+/* Optional per-step trace of a sweep (device memory): entry s of instance b at
+ * [b * capacity + s] for s < capacity: the applied relocation id (j << 13) | y, y the
+ * node j now precedes (a mission, or n_missions + k at the end of route k), or
+ * ASCHED_NULL_MOVE; and the objective after the step. move or z may be NULL. */
+typedef struct {
+  uint32_t* move;
+  int32_t* z;
+  int32_t capacity;
+} asched_sweep_trace;
+
+/* Queue the sweep `algorithm` on every instance of `batch` on `stream`. params:
+ * tenure (Algorithm 3), iterations = the most sweeps (>= 0), cap_mode, lambda,
+ * cluster_size 0 or 1, block_threads 0 (automatic) or a multiple of 32 in [32, 512],
+ * flags: ASCHED_SWEEP_ACCEPT_WORSE (Algorithm 3 only) and ASCHED_SWEEP_REPAIR; timeout_ns
+ * is unused (the sweep waits on nothing). iterations * n_missions + tenure must stay below 2^31.
+ * out is laid out as for asched_solve_batch (flight and overflow may be NULL); trace
+ * may be NULL. Instances whose state does not fit one CTA's shared memory return
+ * ASCHED_E_TOO_LARGE (a paper-sized instance needs about 4 KB). */
+int asched_sweep_batch(const asched_batch* batch, int32_t algorithm, const asched_params* params,
+                       const asched_batch_result* out, const asched_sweep_trace* trace, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -85,11 +85,13 @@ def lib():
             L.orc_tabu_search.argtypes = [P, ctypes.c_int32, ctypes.c_int32, P, P, P, P, P, P,
                                           P, P]
             L.orc_neighbourhood_search.restype = ctypes.c_int32
-            L.orc_neighbourhood_search.argtypes = [P, ctypes.c_int32, P, P, P, P, P, P, P, P,
-                                                   ctypes.c_int64]
+            L.orc_greedy_init_repair.restype = ctypes.c_int32
+            L.orc_greedy_init_repair.argtypes = [P, P, P]
+            L.orc_neighbourhood_search.argtypes = [P, ctypes.c_int32, ctypes.c_int32, P, P, P, P, P,
+                                                   P, P, P, ctypes.c_int64]
             L.orc_tabu_sweep.restype = ctypes.c_int32
-            L.orc_tabu_sweep.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P,
-                                         P, P, P, P, P, P, ctypes.c_int64]
+            L.orc_tabu_sweep.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32, P, P, P, P, P, P, P, P, ctypes.c_int64]
             _lib = L
     return _lib
 
@@ -143,11 +145,12 @@ def feasible(pb: Problem, off, route) -> bool:
     return bool(lib().orc_feasible(pb.ref, _ptr(off), _ptr(route)))
 
 
-def greedy_init(pb: Problem):
-    """Algorithm 1 (reading R8). Returns (status, route_off, route)."""
+def greedy_init(pb: Problem, repair: bool = False):
+    """Algorithm 1 (reading R8; with repair, R9). Returns (status, route_off, route)."""
     off = np.zeros(pb.V + 1, dtype=np.int32)
     route = np.zeros(max(pb.M, 1), dtype=np.int32)
-    rc = lib().orc_greedy_init(pb.ref, _ptr(off), _ptr(route))
+    fn = lib().orc_greedy_init_repair if repair else lib().orc_greedy_init
+    rc = fn(pb.ref, _ptr(off), _ptr(route))
     return int(rc), off, route[:pb.M]
 
 
@@ -222,14 +225,17 @@ def _sweep(pb: Problem, fn, args, init, trace_cap):
             "trace_move": moves[:n], "trace_z": zs[:n]}
 
 
-def neighbourhood_search(pb: Problem, max_sweeps: int, init=None, trace_cap: int = 1 << 16):
-    """Algorithm 2 (readings S1-S3, S5 in the C file). One trace entry per mission step."""
-    return _sweep(pb, lib().orc_neighbourhood_search, (int(max_sweeps),), init, trace_cap)
+def neighbourhood_search(pb: Problem, max_sweeps: int, repair: bool = False, init=None,
+                         trace_cap: int = 1 << 16):
+    """Algorithm 2 (readings S1-S3, S5 in the C file) from Algorithm 1 (R8, or R9 with
+    repair). One trace entry per mission step."""
+    return _sweep(pb, lib().orc_neighbourhood_search, (int(max_sweeps), int(bool(repair))), init,
+                  trace_cap)
 
 
-def tabu_sweep(pb: Problem, tenure: int, max_sweeps: int, accept_worse: bool = False, init=None,
-               trace_cap: int = 1 << 16):
+def tabu_sweep(pb: Problem, tenure: int, max_sweeps: int, accept_worse: bool = False,
+               repair: bool = False, init=None, trace_cap: int = 1 << 16):
     """Algorithm 3 as printed: per-mission sweep with a tabu list (readings S1, S2, S4 or,
     with accept_worse, S4b; S5)."""
-    return _sweep(pb, lib().orc_tabu_sweep, (int(tenure), int(max_sweeps), int(bool(accept_worse))),
-                  init, trace_cap)
+    return _sweep(pb, lib().orc_tabu_sweep, (int(tenure), int(max_sweeps), int(bool(accept_worse)),
+                                             int(bool(repair))), init, trace_cap)

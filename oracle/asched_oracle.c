@@ -50,6 +50,11 @@
  *       least increase of the objective among the vehicles that stay feasible,
  *       ties to the lowest vehicle index. No feasible vehicle is an error (the
  *       paper's swap repair is not taken).
+ *   R9  Algorithm 1's repair, an option used by the sweeps (Section 4.1 leaves it to
+ *       "mission swaps" of Algorithm 2 and a retry): when no vehicle can take mission m
+ *       and some mission is already placed, one sweep of Algorithm 2 (readings S1-S3)
+ *       runs over the partial schedule, and m is tried once more if the sweep moved
+ *       anything. No vehicle after that, or no mission placed yet, is the error.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -195,6 +200,20 @@ static int route_deadlines_ok(const orc_instance *in, int v, const int32_t *ms, 
     end = in->delivery[m];
   }
   return dep + tt(in, ty, end, b) <= in->horizon;
+}
+
+/* The per-route constraints alone: compatibility (con9, R3), deadlines (con7/con8,
+ * R4) and in HARD mode the duty cap (con6). Also meaningful for a partial schedule
+ * (Algorithm 1 while it still places missions). */
+static int routes_feasible(const orc_instance *in, const sched *s) {
+  for (int v = 0; v < s->V; v++) {
+    const int32_t *ms = s->seq + (int64_t)v * s->M;
+    for (int k = 0; k < s->len[v]; k++)
+      if (in->heli_only && in->heli_only[ms[k]] && in->veh_type[v] != 0) return 0;
+    if (!route_deadlines_ok(in, v, ms, s->len[v])) return 0;
+    if (in->cap_mode == ORC_HARD && route_flight(in, v, ms, s->len[v]) > in->duty_cap) return 0;
+  }
+  return 1;
 }
 
 /* Whole-schedule feasibility: every mission exactly once (con1/con2), compatibility
@@ -355,7 +374,99 @@ int32_t orc_feasible(const orc_instance *in, const int32_t *off, const int32_t *
 }
 
 /* Algorithm 1 under reading R8. */
-int32_t orc_greedy_init(const orc_instance *in, int32_t *off_out, int32_t *route_out) {
+/* State of the per-mission sweeps (Algorithms 2 and 3, readings S1-S5 below). */
+typedef struct {
+  int use_tabu, accept_worse;
+  int32_t tenure;
+  int64_t *tabu; /* [M][V]: step through which (mission, vehicle) is tabu, or NULL */
+  int64_t step, n_moves, best_step, z, z_best;
+  sched *best; /* copy of the best schedule met, or NULL */
+  uint32_t *trace_move;
+  int64_t *trace_z;
+  int64_t trace_cap;
+} sweep_ctx;
+
+/* One sweep over s (readings S1, S2 and S3 / S4 / S4b). s may be partial: missions that
+ * Algorithm 1 has not placed yet are absent and play no part. Returns 1 when a move was
+ * applied. */
+static int sweep_pass(const orc_instance *in, sched *s, sched *t, int32_t *snap, sweep_ctx *c) {
+  int M = s->M, V = s->V, applied = 0;
+  for (int i = 0; i < V; i++) {
+    int ni = s->len[i];
+    memcpy(snap, s->seq + (int64_t)i * M, sizeof(int32_t) * (size_t)ni);
+    for (int jj = 0; jj < ni; jj++) {
+      int j = snap[jj], vj, kj;
+      uint32_t rec = ORC_NULL_MOVE;
+      if (locate(s, j, &vj, &kj) && vj == i) {
+        int best_k = -1, best_q = -1;
+        int64_t best_d = 0;
+        for (int k = 0; k < V; k++) {
+          if (k == i) continue;
+          if (in->heli_only && in->heli_only[j] && in->veh_type[k] != 0) continue;
+          if (c->use_tabu && c->tabu[(int64_t)j * V + k] >= c->step) continue; /* S4 */
+          for (int q = 0; q <= s->len[k]; q++) {
+            sched_copy(t, s);
+            remove_at(t, i, kj);
+            insert_at(t, k, q, j);
+            if (!routes_feasible(in, t)) break; /* S2 */
+            int64_t d = sched_cost(in, t, NULL, NULL) - c->z;
+            if (best_k < 0 || d < best_d) {
+              best_k = k;
+              best_q = q;
+              best_d = d;
+            }
+          }
+        }
+        if (best_k >= 0 && (best_d < 0 || c->accept_worse)) {
+          int y = best_q < s->len[best_k] ? s->seq[(int64_t)best_k * M + best_q] : M + best_k;
+          remove_at(s, i, kj);
+          insert_at(s, best_k, best_q, j);
+          c->z = sched_cost(in, s, NULL, NULL);
+          if (c->use_tabu) c->tabu[(int64_t)j * V + i] = c->step + c->tenure;
+          rec = ((uint32_t)j << 13) | (uint32_t)y;
+          c->n_moves++;
+          applied = 1;
+          if (c->z < c->z_best) {
+            c->z_best = c->z;
+            c->best_step = c->step;
+            if (c->best) sched_copy(c->best, s);
+          }
+        }
+      }
+      if (c->step < c->trace_cap) {
+        if (c->trace_move) c->trace_move[c->step] = rec;
+        if (c->trace_z) c->trace_z[c->step] = c->z;
+      }
+      c->step++;
+    }
+  }
+  return applied;
+}
+
+/* The vehicle Algorithm 1 appends mission m to: least objective increase among the
+ * vehicles whose route stays feasible, ties to the lowest index; -1 when none. */
+static int greedy_pick(const orc_instance *in, const sched *s, sched *t, int m) {
+  int best_v = -1;
+  int64_t best_score = 0;
+  int64_t z_before = sched_cost(in, s, NULL, NULL);
+  for (int v = 0; v < s->V; v++) {
+    sched_copy(t, s);
+    insert_at(t, v, t->len[v], m);
+    const int32_t *ms = t->seq + (int64_t)v * s->M;
+    if (in->heli_only && in->heli_only[m] && in->veh_type[v] != 0) continue;
+    if (!route_deadlines_ok(in, v, ms, t->len[v])) continue;
+    if (in->cap_mode == ORC_HARD && route_flight(in, v, ms, t->len[v]) > in->duty_cap) continue;
+    int64_t score = sched_cost(in, t, NULL, NULL) - z_before;
+    if (best_v < 0 || score < best_score) {
+      best_v = v;
+      best_score = score;
+    }
+  }
+  return best_v;
+}
+
+/* Algorithm 1 (reading R8, and R9 when `repair` is set). */
+static int greedy_core(const orc_instance *in, int repair, int32_t *off_out, int32_t *route_out) {
   int rc = check_instance(in);
   if (rc != ORC_OK) return rc;
   int M = in->n_missions, V = in->n_vehicles;
@@ -364,6 +475,7 @@ int32_t orc_greedy_init(const orc_instance *in, int32_t *off_out, int32_t *route
   /* Mission order: heli-only first, then by deadline, then by id (plain selection sort). */
   int *order = (int *)malloc(sizeof(int) * (size_t)(M > 0 ? M : 1));
   int *used = (int *)calloc((size_t)(M > 0 ? M : 1), sizeof(int));
+  int32_t *snap = (int32_t *)malloc(sizeof(int32_t) * (size_t)(M > 0 ? M : 1));
   for (int k = 0; k < M; k++) {
     int best = -1;
     for (int m = 0; m < M; m++) {
@@ -379,32 +491,34 @@ int32_t orc_greedy_init(const orc_instance *in, int32_t *off_out, int32_t *route
   rc = ORC_OK;
   for (int k = 0; k < M && rc == ORC_OK; k++) {
     int m = order[k];
-    int best_v = -1;
-    int64_t best_score = 0;
-    int64_t z_before = sched_cost(in, &s, NULL, NULL);
-    for (int v = 0; v < V; v++) {
-      sched_copy(&t, &s);
-      insert_at(&t, v, t.len[v], m);
-      /* Only the vehicles that keep the partial schedule feasible qualify. */
-      const int32_t *ms = t.seq + (int64_t)v * M;
-      if (in->heli_only && in->heli_only[m] && in->veh_type[v] != 0) continue;
-      if (!route_deadlines_ok(in, v, ms, t.len[v])) continue;
-      if (in->cap_mode == ORC_HARD && route_flight(in, v, ms, t.len[v]) > in->duty_cap) continue;
-      int64_t score = sched_cost(in, &t, NULL, NULL) - z_before;
-      if (best_v < 0 || score < best_score) {
-        best_v = v;
-        best_score = score;
-      }
+    int v = greedy_pick(in, &s, &t, m);
+    if (v < 0 && repair && k > 0) {
+      /* R9: one sweep of Algorithm 2 over the partial schedule, then one more try. */
+      sweep_ctx c = {0};
+      c.best_step = -1;
+      c.z = c.z_best = sched_cost(in, &s, NULL, NULL);
+      if (sweep_pass(in, &s, &t, snap, &c)) v = greedy_pick(in, &s, &t, m);
     }
-    if (best_v < 0) rc = ORC_E_INFEASIBLE_INIT;
-    else insert_at(&s, best_v, s.len[best_v], m);
+    if (v < 0) rc = ORC_E_INFEASIBLE_INIT;
+    else insert_at(&s, v, s.len[v], m);
   }
   if (rc == ORC_OK) sched_to_csr(&s, off_out, route_out);
   free(order);
   free(used);
+  free(snap);
   sched_free(&s);
   sched_free(&t);
   return rc;
+}
+
+/* Algorithm 1 as read in R8 (no repair). */
+int32_t orc_greedy_init(const orc_instance *in, int32_t *off_out, int32_t *route_out) {
+  return greedy_core(in, 0, off_out, route_out);
+}
+
+/* Algorithm 1 with the repair of R9. */
+int32_t orc_greedy_init_repair(const orc_instance *in, int32_t *off_out, int32_t *route_out) {
+  return greedy_core(in, 1, off_out, route_out);
 }
 
 /* Every canonical move of a schedule: delta = Z(after) - Z(before), flags (feasible,
@@ -563,7 +677,7 @@ int32_t orc_tabu_search(const orc_instance *in, int32_t tenure, int32_t iteratio
  * ------------------------------------------------------------------------------------ */
 
 static int sweep_search(const orc_instance *in, int use_tabu, int accept_worse, int32_t tenure,
-                        int32_t max_sweeps,
+                        int32_t max_sweeps, int repair,
                         const int32_t *init_off, const int32_t *init_route, int32_t *best_off,
                         int32_t *best_route, int64_t *z_best_out, int32_t *counts_out,
                         uint32_t *trace_move, int64_t *trace_z, int64_t trace_cap) {
@@ -584,81 +698,40 @@ static int sweep_search(const orc_instance *in, int use_tabu, int accept_worse, 
     if (sched_from_csr(&s, off, route) != ORC_OK || !orc_feasible(in, off, route))
       rc = ORC_E_INFEASIBLE_INIT;
   } else {
-    rc = orc_greedy_init(in, off, route);
+    rc = greedy_core(in, repair, off, route);
   }
-  int64_t sweeps = 0, n_moves = 0, step = 0, best_step = -1;
-  int64_t z = 0, z_best = 0, z_init = 0;
+  sweep_ctx c = {0};
+  int64_t sweeps = 0, z_init = 0;
   if (rc == ORC_OK) {
     sched_from_csr(&s, off, route);
     for (int64_t x = 0; x < (int64_t)(M > 0 ? M : 1) * V; x++) tabu[x] = -1;
-    z = sched_cost(in, &s, NULL, NULL);
-    z_best = z_init = z;
+    c.use_tabu = use_tabu;
+    c.accept_worse = accept_worse;
+    c.tenure = tenure;
+    c.tabu = tabu;
+    c.best_step = -1;
+    c.z = c.z_best = z_init = sched_cost(in, &s, NULL, NULL);
+    c.best = &best_t;
+    c.trace_move = trace_move;
+    c.trace_z = trace_z;
+    c.trace_cap = trace_cap;
     sched_copy(&best_t, &s);
     int go_on = 1;
     while (go_on && sweeps < max_sweeps) {
-      int applied = 0;
-      int64_t z_best_before = z_best;
-      for (int i = 0; i < V; i++) {
-        int ni = s.len[i];
-        memcpy(snap, s.seq + (int64_t)i * M, sizeof(int32_t) * (size_t)ni);
-        for (int jj = 0; jj < ni; jj++) {
-          int j = snap[jj], vj, kj;
-          uint32_t rec = ORC_NULL_MOVE;
-          if (locate(&s, j, &vj, &kj) && vj == i) {
-            int best_k = -1, best_q = -1;
-            int64_t best_d = 0;
-            for (int k = 0; k < V; k++) {
-              if (k == i) continue;
-              if (in->heli_only && in->heli_only[j] && in->veh_type[k] != 0) continue;
-              if (use_tabu && tabu[(int64_t)j * V + k] >= step) continue; /* S4 */
-              for (int q = 0; q <= s.len[k]; q++) {
-                sched_copy(&t, &s);
-                remove_at(&t, i, kj);
-                insert_at(&t, k, q, j);
-                if (!sched_feasible(in, &t)) break; /* S2 */
-                int64_t d = sched_cost(in, &t, NULL, NULL) - z;
-                if (best_k < 0 || d < best_d) {
-                  best_k = k;
-                  best_q = q;
-                  best_d = d;
-                }
-              }
-            }
-            if (best_k >= 0 && (best_d < 0 || accept_worse)) {
-              int y = best_q < s.len[best_k] ? s.seq[(int64_t)best_k * M + best_q] : M + best_k;
-              remove_at(&s, i, kj);
-              insert_at(&s, best_k, best_q, j);
-              z = sched_cost(in, &s, NULL, NULL);
-              if (use_tabu) tabu[(int64_t)j * V + i] = step + tenure;
-              rec = ((uint32_t)j << 13) | (uint32_t)y;
-              n_moves++;
-              applied = 1;
-              if (z < z_best) {
-                z_best = z;
-                best_step = step;
-                sched_copy(&best_t, &s);
-              }
-            }
-          }
-          if (step < trace_cap) {
-            if (trace_move) trace_move[step] = rec;
-            if (trace_z) trace_z[step] = z;
-          }
-          step++;
-        }
-      }
+      int64_t z_best_before = c.z_best;
+      int applied = sweep_pass(in, &s, &t, snap, &c);
       sweeps++;
-      go_on = accept_worse ? (z_best < z_best_before) : applied;
+      go_on = accept_worse ? (c.z_best < z_best_before) : applied;
     }
     sched_to_csr(&best_t, best_off, best_route);
   }
-  *z_best_out = z_best;
-  counts_out[0] = (int32_t)sweeps;
-  counts_out[1] = (int32_t)n_moves;
-  counts_out[2] = (int32_t)step;
-  counts_out[3] = (int32_t)best_step;
+  z_best_out[0] = c.z_best;
   z_best_out[1] = z_init;
-  z_best_out[2] = z;
+  z_best_out[2] = c.z;
+  counts_out[0] = (int32_t)sweeps;
+  counts_out[1] = (int32_t)c.n_moves;
+  counts_out[2] = (int32_t)c.step;
+  counts_out[3] = (int32_t)(rc == ORC_OK ? c.best_step : -1);
   free(off);
   free(route);
   free(tabu);
@@ -669,21 +742,24 @@ static int sweep_search(const orc_instance *in, int use_tabu, int accept_worse, 
   return rc;
 }
 
-/* Algorithm 2 (readings S1-S3, S5). z_out[3] = {best, initial, final} objectives;
+/* Algorithm 2 (readings S1-S3, S5), started from Algorithm 1 (with the repair of R9
+ * when `repair` is set) unless init_off / init_route give the start.
+ * z_out[3] = {best, initial, final} objectives;
  * counts_out[4] = {sweeps, moves applied, steps, step of the best (-1: initial)}. */
-int32_t orc_neighbourhood_search(const orc_instance *in, int32_t max_sweeps, const int32_t *init_off,
+int32_t orc_neighbourhood_search(const orc_instance *in, int32_t max_sweeps, int32_t repair,
+                                 const int32_t *init_off,
                                  const int32_t *init_route, int32_t *best_off, int32_t *best_route,
                                  int64_t *z_out, int32_t *counts_out, uint32_t *trace_move,
                                  int64_t *trace_z, int64_t trace_cap) {
-  return sweep_search(in, 0, 0, 0, max_sweeps, init_off, init_route, best_off, best_route, z_out,
+  return sweep_search(in, 0, 0, 0, max_sweeps, repair, init_off, init_route, best_off, best_route, z_out,
                       counts_out, trace_move, trace_z, trace_cap);
 }
 
 /* Algorithm 3 as printed (readings S1, S2, S4 or S4b, S5); outputs as above. */
 int32_t orc_tabu_sweep(const orc_instance *in, int32_t tenure, int32_t max_sweeps, int32_t accept_worse,
-                       const int32_t *init_off,
+                       int32_t repair, const int32_t *init_off,
                        const int32_t *init_route, int32_t *best_off, int32_t *best_route, int64_t *z_out,
                        int32_t *counts_out, uint32_t *trace_move, int64_t *trace_z, int64_t trace_cap) {
-  return sweep_search(in, 1, accept_worse != 0, tenure, max_sweeps, init_off, init_route, best_off, best_route, z_out,
+  return sweep_search(in, 1, accept_worse != 0, tenure, max_sweeps, repair, init_off, init_route, best_off, best_route, z_out,
                       counts_out, trace_move, trace_z, trace_cap);
 }

@@ -86,6 +86,17 @@ class BatchResult(ctypes.Structure):
     _fields_ = [("route_off", P), ("route", P), ("flight", P), ("overflow", P), ("info", P)]
 
 
+class SweepTrace(ctypes.Structure):
+    _fields_ = [("move", P), ("z", P), ("capacity", ctypes.c_int32)]
+
+
+SWEEP_NEIGHBOURHOOD = 2  # Algorithm 2
+SWEEP_TABU = 3  # Algorithm 3 as printed
+SWEEP_ACCEPT_WORSE = 4  # asched_params.flags bits for the sweeps
+SWEEP_REPAIR = 8
+INFO_MOVES, INFO_STEPS = 6, 7
+
+
 # Every entry point of include/asched.h with its ctypes signature.
 SIGNATURES = {
     "asched_abi_version": (ctypes.c_int, []),
@@ -102,6 +113,7 @@ SIGNATURES = {
     "asched_server_sizes": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_int32, P, P]),
     "asched_serve": (ctypes.c_int, [P, P, ctypes.c_int64, ctypes.c_int32, P]),
+    "asched_sweep_batch": (ctypes.c_int, [P, ctypes.c_int32, P, P, P, P]),
 }
 
 _lock = threading.Lock()

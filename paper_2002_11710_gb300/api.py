@@ -18,6 +18,7 @@ from ._lib import (COMPACT_LAYOUT, E_CUDA, E_INFEASIBLE_INIT, E_INVALID, E_OVERF
                    E_TOO_LARGE, FLAG_ADMISSIBLE, FLAG_ASPIRATION, FLAG_FEASIBLE, FLAG_TABU, HARD,
                    INFO_BEST_IT, INFO_ITERS, INFO_LEN, INFO_STATUS, INFO_Z_BEST, INFO_Z_FINAL,
                    INFO_Z_INIT, NULL_MOVE, OK, PENALTY, SWAP_BIT, AschedError)
+from ._lib import INFO_MOVES, INFO_STEPS, SWEEP_ACCEPT_WORSE, SWEEP_NEIGHBOURHOOD, SWEEP_REPAIR, SWEEP_TABU  # noqa: F401
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -407,3 +408,43 @@ def capture_batch(bp: BatchProblem, params: _lib.Params, out: Optional[BatchOutp
     with torch.cuda.graph(g, stream=s):
         solve_batch(bp, params, out=out, stream=s)
     return g, out
+
+
+def sweep_params(max_sweeps: int, cap_mode: int = HARD, lam: int = 1000, tenure: int = 0,
+                 accept_worse: bool = False, block_threads: int = 0, repair: bool = False) -> _lib.Params:
+    """Parameters of asched_sweep_batch: iterations holds the most sweeps; repair turns on
+    Algorithm 1's repair sweep."""
+    flags = (SWEEP_ACCEPT_WORSE if accept_worse else 0) | (SWEEP_REPAIR if repair else 0)
+    return _lib.Params(int(tenure), int(max_sweeps), int(cap_mode), int(lam), 0, int(block_threads), 0,
+                       flags)
+
+
+@dataclasses.dataclass
+class SweepTrace:
+    move: torch.Tensor  # uint32 ids stored as int32, [B][capacity]
+    z: torch.Tensor  # int32 [B][capacity]
+    capacity: int
+
+    def struct(self):
+        return _lib.SweepTrace(_ptr(self.move), _ptr(self.z), int(self.capacity))
+
+
+def sweep_batch(bp: BatchProblem, algorithm: int, params: _lib.Params, out: Optional[BatchOutput] = None,
+                trace_capacity: int = 0, stream: Optional[torch.cuda.Stream] = None):
+    """Queue asched_sweep_batch: Algorithm 2 (SWEEP_NEIGHBOURHOOD) or the per-mission sweep
+    of Algorithm 3 (SWEEP_TABU) on every instance. Returns (out, trace or None)."""
+    if out is None:
+        out = bp.alloc_output()
+    trace = None
+    if trace_capacity > 0:
+        n = max(bp.B, 1) * int(trace_capacity)
+        trace = SweepTrace(torch.zeros(n, dtype=torch.int32, device=bp.device),
+                           torch.zeros(n, dtype=torch.int32, device=bp.device), int(trace_capacity))
+    s = stream if stream is not None else torch.cuda.current_stream(bp.device)
+    res = out.struct()
+    tr = trace.struct() if trace is not None else None
+    rc = _lib.load().asched_sweep_batch(ctypes.byref(bp.struct), int(algorithm), ctypes.byref(params),
+                                        ctypes.byref(res), ctypes.byref(tr) if tr is not None else None,
+                                        ctypes.c_void_p(s.cuda_stream))
+    _lib.check(rc, "asched_sweep_batch")
+    return out, trace

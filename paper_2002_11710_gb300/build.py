@@ -1,7 +1,7 @@
 """Compile the CUDA library in-tree: paper_2002_11710_gb300/_build/libasched.so.
 
-sm_103a only (GB300); one translation unit, so it builds in seconds here and on
-the GPU host alike.
+sm_103a only (GB300); two translation units compiled in parallel and linked into
+one shared library, so it builds in seconds here and on the GPU host alike.
 """
 from __future__ import annotations
 
@@ -11,7 +11,7 @@ import sys
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
-SRC = os.path.join(PKG, "csrc", "asched.cu")
+SRCS = [os.path.join(PKG, "csrc", n) for n in ("asched.cu", "sweep.cu")]
 HDR = os.path.join(ROOT, "include", "asched.h")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libasched.so")
@@ -19,7 +19,7 @@ LIB = os.path.join(OUT_DIR, "libasched.so")
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
     "-O3", "-lineinfo", "-std=c++17",
-    "-Xcompiler", "-fPIC", "-shared",
+    "-Xcompiler", "-fPIC",
 ]
 
 
@@ -30,15 +30,28 @@ def nvcc() -> str:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
-    stale = (not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(SRC),
-                                                                  os.path.getmtime(HDR)))
+    newest = max(os.path.getmtime(x) for x in SRCS + [HDR])
+    stale = not os.path.exists(LIB) or os.path.getmtime(LIB) < newest
     if force or stale:
-        tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc(), *NVCC_FLAGS, "-I", os.path.join(ROOT, "include"), "-o", tmp, SRC]
-        if verbose:
-            cmd.insert(1, "-Xptxas=-v")
-            print(" ".join(cmd), file=sys.stderr)
-        subprocess.check_call(cmd)
+        tag = f".tmp{os.getpid()}"
+        inc = ["-I", os.path.join(ROOT, "include")]
+        objs, procs = [], []
+        for src in SRCS:
+            obj = os.path.join(OUT_DIR, os.path.basename(src) + tag + ".o")  # nvcc reads the suffix
+            cmd = [nvcc(), *NVCC_FLAGS, *inc, "-c", "-o", obj, src]
+            if verbose:
+                cmd.insert(1, "-Xptxas=-v")
+                print(" ".join(cmd), file=sys.stderr)
+            objs.append(obj)
+            procs.append(subprocess.Popen(cmd))
+        codes = [p.wait() for p in procs]
+        if any(codes):
+            raise subprocess.CalledProcessError(next(c for c in codes if c), "nvcc")
+        tmp = os.path.join(OUT_DIR, "libasched" + tag + ".so")
+        subprocess.check_call([nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-shared",
+                               "-o", tmp, *objs])
+        for obj in objs:
+            os.remove(obj)
         os.replace(tmp, LIB)
     return LIB
 

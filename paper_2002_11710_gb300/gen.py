@@ -150,12 +150,19 @@ def make_instance(seed: int, *, n_bases: int, n_vehicles: int, n_facilities: int
                   pairs: str = "uniform", zipf_s: float = 1.1, speed_kmh: float = 250.0,
                   duty_cap: int = 720, horizon: int = 1440, plane_speed_kmh: Optional[float] = None,
                   n_planes: int = 0, heli_only_frac: float = 0.0, deadlines: bool = False,
-                  deadline_lo: int = 0, name: str = "") -> Instance:
+                  deadline_lo: int = 0, deadline_window: bool = False, name: str = "") -> Instance:
     """Draw one instance; see the module docstring for the fixed draw order.
 
     With ``plane_speed_kmh`` set there are two travel layers (type 0 helicopter at
     ``speed_kmh``, type 1 plane at ``plane_speed_kmh``) and the first ``n_planes``
     bases hold planes, as in the paper's 4 plane + 8 helicopter fleet (Section 5).
+
+    ``deadline_window``: instead of uniform in [deadline_lo, horizon], each mission's
+    arrive-by time is drawn inside a window that some vehicle allowed to fly it can meet
+    on its own (leave base at 0, arrive by w, be home by the horizon): one compatible
+    vehicle with a non-empty window is drawn uniformly, then w uniformly in it. Every
+    mission is then feasible alone (the paper only kept valid scenarios, Section 5);
+    together they may still not be.
     """
     rng = np.random.default_rng(seed)
     base_xy = _uniform_points(rng, n_bases, box_km)
@@ -185,8 +192,26 @@ def make_instance(seed: int, *, n_bases: int, n_vehicles: int, n_facilities: int
     if heli_only_frac > 0.0:
         heli = (rng.random(n_missions) < heli_only_frac).astype(np.int32)
     dl = None
-    if deadlines:
+    if deadlines and not deadline_window:
         dl = rng.integers(deadline_lo, horizon + 1, size=n_missions).astype(np.int32)
+    elif deadlines:
+        dl = np.zeros(n_missions, dtype=np.int32)
+        pk, dv = p + n_bases, d + n_bases
+        for j in range(n_missions):
+            wins = []
+            for v in range(n_vehicles):
+                if heli is not None and heli[j] and veh_type[v] != 0:
+                    continue
+                T = travel[veh_type[v]]
+                b = veh_base[v]
+                lo = max(deadline_lo, int(T[b, pk[j]]) + int(T[pk[j], dv[j]]))
+                hi = horizon - int(T[dv[j], b])
+                if lo <= hi:
+                    wins.append((lo, hi))
+            if not wins:
+                raise ValueError(f"mission {j} fits no vehicle within the horizon")
+            lo, hi = wins[int(rng.integers(len(wins)))]
+            dl[j] = int(rng.integers(lo, hi + 1))
     return Instance(
         travel=travel,
         veh_base=veh_base,
@@ -262,6 +287,18 @@ def paper_model(seed: int, n_missions: int, *, heli_only_frac: float = 0.3,
                          heli_only_frac=heli_only_frac, deadlines=deadlines,
                          deadline_lo=240, duty_cap=600, name=f"paper-model-s{seed}-m{n_missions}")
 
+
+
+def paper_fleet(seed: int, n_missions: int, *, heli_only_frac: float = 0.3) -> Instance:
+    """The paper's fleet as paper_model, with arrive-by times drawn inside windows a
+    compatible vehicle can meet (``deadline_window``), so that no mission is infeasible
+    on its own. The workload of the paper's own sweeps (Algorithms 2 and 3)."""
+    return make_instance(seed, n_bases=12, n_vehicles=12, n_facilities=40,
+                         n_missions=n_missions, box_km=1000.0, geography="clustered",
+                         speed_kmh=300.0, plane_speed_kmh=500.0, n_planes=4,
+                         heli_only_frac=heli_only_frac, deadlines=True, deadline_lo=240,
+                         deadline_window=True, duty_cap=600,
+                         name=f"paper-fleet-s{seed}-m{n_missions}")
 
 
 def random_instance(seed: int, *, n_loc: int, n_vehicles: int, n_missions: int,

@@ -44,3 +44,35 @@ def test_workload_batches_pack():
                                                              n_types=2)]):
         bp = api.BatchProblem(insts, device="cpu")
         assert bp.B == len(insts)
+
+
+def test_sweep_host_argument_errors_need_no_gpu():
+    """asched_sweep_batch rejects bad arguments on the host before any CUDA call."""
+    import ctypes
+
+    from paper_2002_11710_gb300 import _lib
+    insts = [gen.random_instance(s, n_loc=6, n_vehicles=2, n_missions=4) for s in range(3)]
+    bp = api.BatchProblem(insts, device="cpu")
+    out = bp.alloc_output().struct()
+    L = _lib.load()
+
+    def call(alg, p, trace=None):
+        return L.asched_sweep_batch(ctypes.byref(bp.struct), alg, ctypes.byref(p), ctypes.byref(out),
+                                    ctypes.byref(trace) if trace is not None else None, None)
+
+    assert call(9, api.sweep_params(5)) == api.E_INVALID
+    assert call(api.SWEEP_NEIGHBOURHOOD, api.sweep_params(5, accept_worse=True)) == api.E_INVALID
+    assert call(api.SWEEP_TABU, api.sweep_params(5, block_threads=48)) == api.E_INVALID
+    assert call(api.SWEEP_TABU, api.sweep_params(5, block_threads=1024)) == api.E_INVALID
+    assert call(api.SWEEP_TABU, api.sweep_params(-1)) == api.E_INVALID
+    assert call(api.SWEEP_TABU, api.sweep_params(5, cap_mode=7)) == api.E_INVALID
+    p = api.sweep_params(5)
+    p.cluster_size = 2
+    assert call(api.SWEEP_TABU, p) == api.E_INVALID
+    p = api.sweep_params(5)
+    p.flags = api.COMPACT_LAYOUT
+    assert call(api.SWEEP_TABU, p) == api.E_INVALID
+    assert call(api.SWEEP_TABU, api.sweep_params(5), _lib.SweepTrace(None, None, -1)) == api.E_INVALID
+    empty = api.BatchProblem([], device="cpu")
+    assert L.asched_sweep_batch(ctypes.byref(empty.struct), api.SWEEP_TABU, ctypes.byref(api.sweep_params(5)),
+                                ctypes.byref(empty.alloc_output().struct()), None, None) == api.OK

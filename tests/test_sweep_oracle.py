@@ -101,54 +101,102 @@ def _compatible(inst, m, k):
     return inst.heli_only is None or not int(inst.heli_only[m]) or int(inst.veh_type[k]) == 0
 
 
+def _partial_ok(inst, routes, mode):
+    """con1-con11 on the missions placed so far (the sub-instance of those missions)."""
+    placed = sorted(m for r in routes for m in r)
+    remap = {m: i for i, m in enumerate(placed)}
+    return ilp.feasible(inst.subinstance(placed), tuple(tuple(remap[m] for m in r) for r in routes), mode)
+
+
+def _pass(inst, mode, lam, routes, st, is_tabu, tenure, accept_worse):
+    """One sweep (S1, S2, S3 / S4 / S4b) on explicit, possibly partial, schedules;
+    st holds z, z_best, best, tabu and the trace. Returns whether a move was applied."""
+    M, V = inst.n_missions, inst.n_vehicles
+    applied = False
+    for i in range(V):
+        for j in list(routes[i]):
+            rec = NULL
+            if j in routes[i]:
+                kj = routes[i].index(j)
+                cands = []
+                for k in range(V):
+                    if k == i or not _compatible(inst, j, k):
+                        continue
+                    if is_tabu and st["tabu"].get((j, k), -1) >= len(st["trace"]):
+                        continue
+                    for q in range(len(routes[k]) + 1):
+                        t = [list(r) for r in routes]
+                        del t[i][kj]
+                        t[k].insert(q, j)
+                        if not _partial_ok(inst, t, mode):
+                            break
+                        cands.append((ilp.objective(inst, tuple(map(tuple, t)), mode, lam) - st["z"], k, q))
+                if cands:
+                    d, k, q = min(cands)
+                    if d < 0 or accept_worse:
+                        y = routes[k][q] if q < len(routes[k]) else M + k
+                        del routes[i][kj]
+                        routes[k].insert(q, j)
+                        st["z"] += d
+                        if is_tabu:
+                            st["tabu"][(j, i)] = len(st["trace"]) + tenure
+                        rec = (j << 13) | y
+                        applied = True
+                        if st["z"] < st["z_best"]:
+                            st["z_best"], st["best"] = st["z"], [list(r) for r in routes]
+            st["trace"].append((rec, st["z"]))
+    return applied
+
+
+def _state(inst, routes, mode, lam):
+    z = ilp.objective(inst, tuple(map(tuple, routes)), mode, lam)
+    return {"z": z, "z_best": z, "best": [list(r) for r in routes], "tabu": {}, "trace": []}
+
+
 def _rederive(inst, mode, lam, routes, is_tabu, tenure, accept_worse, max_sweeps):
     """Algorithm 2/3 re-derived step by step on explicit schedules (readings S1-S5)."""
-    M, V = inst.n_missions, inst.n_vehicles
-    z = ilp.objective(inst, tuple(map(tuple, routes)), mode, lam)
-    z_best, best = z, [list(r) for r in routes]
-    tabu = {}
-    trace = []
+    st = _state(inst, routes, mode, lam)
     sweeps = 0
     go_on = True
     while go_on and sweeps < max_sweeps:
-        applied = False
-        zb0 = z_best
-        for i in range(V):
-            for j in list(routes[i]):
-                rec = NULL
-                if j in routes[i]:
-                    kj = routes[i].index(j)
-                    cands = []
-                    for k in range(V):
-                        if k == i or not _compatible(inst, j, k):
-                            continue
-                        if is_tabu and tabu.get((j, k), -1) >= len(trace):
-                            continue
-                        for q in range(len(routes[k]) + 1):
-                            t = [list(r) for r in routes]
-                            del t[i][kj]
-                            t[k].insert(q, j)
-                            tt = tuple(map(tuple, t))
-                            if not ilp.feasible(inst, tt, mode):
-                                break
-                            cands.append((ilp.objective(inst, tt, mode, lam) - z, k, q))
-                    if cands:
-                        d, k, q = min(cands)
-                        if d < 0 or accept_worse:
-                            y = routes[k][q] if q < len(routes[k]) else M + k
-                            del routes[i][kj]
-                            routes[k].insert(q, j)
-                            z += d
-                            if is_tabu:
-                                tabu[(j, i)] = len(trace) + tenure
-                            rec = (j << 13) | y
-                            applied = True
-                            if z < z_best:
-                                z_best, best = z, [list(r) for r in routes]
-                trace.append((rec, z))
+        zb0 = st["z_best"]
+        applied = _pass(inst, mode, lam, routes, st, is_tabu, tenure, accept_worse)
         sweeps += 1
-        go_on = (z_best < zb0) if accept_worse else applied
-    return trace, z_best, best, sweeps
+        go_on = (st["z_best"] < zb0) if accept_worse else applied
+    return st["trace"], st["z_best"], st["best"], sweeps
+
+
+def _greedy(inst, mode, lam, repair):
+    """Algorithm 1 (R8, and the repair of R9) re-derived on explicit partial schedules."""
+    M, V = inst.n_missions, inst.n_vehicles
+    heli = inst.heli_only
+    dl = inst.deadline
+    order = sorted(range(M), key=lambda m: (0 if heli is not None and heli[m] else 1,
+                                            int(dl[m]) if dl is not None else 0, m))
+    routes = [[] for _ in range(V)]
+
+    def pick(m):
+        z0 = ilp.objective(inst, tuple(map(tuple, routes)), mode, lam)
+        best = None
+        for v in range(V):
+            t = [list(r) for r in routes]
+            t[v].append(m)
+            if not _partial_ok(inst, t, mode):
+                continue
+            sc = ilp.objective(inst, tuple(map(tuple, t)), mode, lam) - z0
+            if best is None or sc < best[0]:
+                best = (sc, v)
+        return best
+
+    for n, m in enumerate(order):
+        b = pick(m)
+        if b is None and repair and n > 0:
+            if _pass(inst, mode, lam, routes, _state(inst, routes, mode, lam), False, 0, False):
+                b = pick(m)
+        if b is None:
+            return None
+        routes[b[1]].append(m)
+    return routes
 
 
 @pytest.mark.parametrize("case", CASES)
@@ -262,3 +310,64 @@ def test_sweep_reports_infeasible_start():
     pb = oracle.Problem(bad, ilp.HARD, 1000)
     assert oracle.neighbourhood_search(pb, 5)["status"] == oracle.E_INFEASIBLE_INIT
     assert oracle.tabu_sweep(pb, 3, 5)["status"] == oracle.E_INFEASIBLE_INIT
+
+
+REPAIR_CASES = [(23, 14, ilp.HARD), (60, 14, ilp.HARD), (72, 18, ilp.HARD), (57, 22, ilp.HARD),
+                (34, 26, ilp.HARD), (96, 30, ilp.PENALTY), (116, 30, ilp.PENALTY)]
+
+
+@pytest.mark.parametrize("case", REPAIR_CASES)
+def test_greedy_repair_rederived(case):
+    """Paper-fleet instances where Algorithm 1 gets stuck and the repair sweep (R9)
+    frees a place: the oracle's start equals the re-derived one."""
+    seed, m, mode = case
+    inst = gen.paper_fleet(seed, m)
+    pb = oracle.Problem(inst, mode, 1000)
+    assert oracle.greedy_init(pb)[0] == oracle.E_INFEASIBLE_INIT
+    assert _greedy(inst, mode, 1000, repair=False) is None
+    rc, off, route = oracle.greedy_init(pb, repair=True)
+    assert rc == 0
+    want = _greedy(inst, mode, 1000, repair=True)
+    assert _routes_of(pb, off, route) == want
+    assert ilp.feasible(inst, tuple(map(tuple, want)), mode)
+
+
+@pytest.mark.parametrize("mode", [ilp.HARD, ilp.PENALTY])
+def test_repair_changes_nothing_when_algorithm_1_succeeds(mode):
+    for seed in range(40):
+        inst = gen.paper_fleet(seed, 12 + seed % 20)
+        pb = oracle.Problem(inst, mode, 1000)
+        a = oracle.greedy_init(pb)
+        b = oracle.greedy_init(pb, repair=True)
+        if a[0] == 0:
+            assert b[0] == 0 and a[1].tolist() == b[1].tolist() and a[2].tolist() == b[2].tolist()
+        else:
+            assert a[0] == oracle.E_INFEASIBLE_INIT
+
+
+@pytest.mark.parametrize("seed", [0, 3, 7])
+def test_plain_greedy_rederived_on_paper_fleet(seed):
+    inst = gen.paper_fleet(seed, 16)
+    for mode in (ilp.HARD, ilp.PENALTY):
+        pb = oracle.Problem(inst, mode, 1000)
+        rc, off, route = oracle.greedy_init(pb)
+        want = _greedy(inst, mode, 1000, repair=False)
+        assert (rc == 0) == (want is not None)
+        if want is not None:
+            assert _routes_of(pb, off, route) == want
+
+
+def test_paper_fleet_deadlines_sit_in_a_vehicle_window():
+    """gen.paper_fleet: every mission can be flown alone by a vehicle allowed to fly it."""
+    for seed in range(10):
+        inst = gen.paper_fleet(seed, 33)
+        for j in range(inst.n_missions):
+            ok = False
+            for v in range(inst.n_vehicles):
+                if not _compatible(inst, j, v):
+                    continue
+                T = inst.travel[inst.veh_type[v]]
+                b, p, d = inst.veh_base[v], inst.pickup[j], inst.delivery[j]
+                w = int(inst.deadline[j])
+                ok |= T[b, p] + T[p, d] <= w and w + T[d, b] <= inst.horizon and w >= 240
+            assert ok
