@@ -248,6 +248,7 @@ def run_gpu(args, rank, world, local_rank):
     e2e_s = max_over_ranks(e2e_s, world, dev)
     batched = run_batched(args, dev) if args.batched else None
     serving = run_serving(args, dev) if args.serve_seconds > 0 else None
+    sweeps = run_sweeps(args, dev) if args.sweeps else None
     if rank != 0:
         return
     value = whole_job_rate(moves_step * args.steps, world, dev_s)
@@ -289,6 +290,7 @@ def run_gpu(args, rank, world, local_rank):
                      "frac_of_sms_used": achieved / (peak_tops * plan.cluster_size / sm_count)},
         "batched": batched,
         "serving": serving,
+        "sweeps": sweeps,
         "cpu_baseline": None if cpu_rate is None else {
             "value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {args.cpu_iterations} of 5,000 iterations, same instance, {cpu_dt:.1f} s"},
@@ -401,6 +403,66 @@ def run_serving(args, dev):
                                                  "p99": float(np.percentile(lat2, 99) * 1e3)}}}
 
 
+def run_sweeps(args, dev):
+    """The paper's own local searches (Algorithm 2, Neighbourhood Search; Algorithm 3 as
+    printed, the per-mission sweep) started from Algorithm 1 with its repair, by default on
+    65,536 paper-fleet instances (16,384 distinct ones, each four times: 12-33 missions,
+    4 plane + 8 helicopter bases, heli-only missions, arrive-by windows, 10 h cap as a
+    constraint), one launch per algorithm; the batch's inputs (3.2 GB) are larger than L2.
+    Against the oracle on one core for 256 of the instances."""
+    import torch
+
+    import oracle
+    from paper_2002_11710_gb300 import api, gen
+
+    rng = np.random.default_rng(5)
+    sizes = rng.integers(12, 34, size=args.sweep_distinct)
+    distinct = [gen.paper_fleet(40_000 + i, int(m)) for i, m in enumerate(sizes)]
+    insts = distinct * args.sweep_copies
+    B = len(insts)
+    bp = api.BatchProblem(insts, dev)
+    out = {"workload": (f"{B:,} paper-fleet instances ({len(distinct):,} distinct x {args.sweep_copies}), "
+                        "M ~ U[12, 33], 12 vehicles (4 planes), HARD 600 min cap, arrive-by windows, "
+                        "Algorithm 1 with repair, at most 100 sweeps, tenure 7"),
+           "gpu_launches": 1}
+    for name, alg in (("algorithm_2", api.SWEEP_NEIGHBOURHOOD), ("algorithm_3", api.SWEEP_TABU)):
+        params = api.sweep_params(100, api.HARD, 1000, 7, repair=True)
+        res, _ = api.sweep_batch(bp, alg, params)
+        for _ in range(max(1, args.warmup // 2)):
+            api.sweep_batch(bp, alg, params, out=res)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(5):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            api.sweep_batch(bp, alg, params, out=res)
+            b.record()
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        info = res.info.view(-1, api.INFO_LEN).cpu().numpy()
+        ok = info[:, api.INFO_STATUS] == 0
+        t = statistics.median(ms)
+        out[name] = {"ms": t, "solves_per_s": B / t * 1e3,
+                     "mission_steps_per_s": float(info[ok, api.INFO_STEPS].sum()) / t * 1e3,
+                     "feasible_start_frac": float(ok.mean()),
+                     "mean_sweeps": float(info[ok, api.INFO_ITERS].mean()),
+                     "mean_improvement_pct": float(100.0 * (1.0 - info[ok, api.INFO_Z_BEST].sum() /
+                                                              info[ok, api.INFO_Z_INIT].sum()))}
+        if _env_int("RANK", 0) == 0 and args.cpu_iterations > 0:
+            t0 = time.perf_counter()
+            for inst in distinct[:256]:
+                pb = oracle.Problem(inst, api.HARD, 1000)
+                if alg == api.SWEEP_NEIGHBOURHOOD:
+                    oracle.neighbourhood_search(pb, 100, repair=True)
+                else:
+                    oracle.tabu_sweep(pb, 7, 100, repair=True)
+            dt = time.perf_counter() - t0
+            out[name]["cpu_oracle"] = {"solves_per_s": 256 / dt, "cores": 1,
+                                       "sample": f"first 256 distinct instances, {dt:.2f} s"}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -414,6 +476,12 @@ def main():
     ap.add_argument("--int32-lanes-per-sm", type=int, default=128)
     ap.add_argument("--no-batched", dest="batched", action="store_false",
                     help="skip the 1,024-instance batched measurement")
+    ap.add_argument("--no-sweeps", dest="sweeps", action="store_false",
+                    help="skip the Algorithm 2 / Algorithm 3 sweep measurement")
+    ap.add_argument("--sweeps-only", action="store_true",
+                    help="run only the sweep measurement and print its JSON object")
+    ap.add_argument("--sweep-distinct", type=int, default=16384)
+    ap.add_argument("--sweep-copies", type=int, default=4)
     ap.add_argument("--serve-seconds", type=float, default=20.0,
                     help="length of the Poisson request stream for the serving measurement "
                          "(the serving workload is 60 s; 0 skips it)")
@@ -423,6 +491,12 @@ def main():
     local_rank = _env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.sweeps_only:
+        import torch
+
+        torch.cuda.set_device(local_rank)
+        print(json.dumps(run_sweeps(args, torch.device("cuda", local_rank))), flush=True)
         return
     if world > 1:
         import torch

@@ -146,7 +146,7 @@ def feasible(pb: Problem, off, route) -> bool:
 
 
 def greedy_init(pb: Problem, repair: bool = False):
-    """Algorithm 1 (reading R8; with repair, R9). Returns (status, route_off, route)."""
+    """Algorithm 1 (reading R8; with repair, R12). Returns (status, route_off, route)."""
     off = np.zeros(pb.V + 1, dtype=np.int32)
     route = np.zeros(max(pb.M, 1), dtype=np.int32)
     fn = lib().orc_greedy_init_repair if repair else lib().orc_greedy_init
@@ -227,7 +227,7 @@ def _sweep(pb: Problem, fn, args, init, trace_cap):
 
 def neighbourhood_search(pb: Problem, max_sweeps: int, repair: bool = False, init=None,
                          trace_cap: int = 1 << 16):
-    """Algorithm 2 (readings S1-S3, S5 in the C file) from Algorithm 1 (R8, or R9 with
+    """Algorithm 2 (readings S1-S3, S5 in the C file) from Algorithm 1 (R8, or R12 with
     repair). One trace entry per mission step."""
     return _sweep(pb, lib().orc_neighbourhood_search, (int(max_sweeps), int(bool(repair))), init,
                   trace_cap)

@@ -50,7 +50,7 @@
  *       least increase of the objective among the vehicles that stay feasible,
  *       ties to the lowest vehicle index. No feasible vehicle is an error (the
  *       paper's swap repair is not taken).
- *   R9  Algorithm 1's repair, an option used by the sweeps (Section 4.1 leaves it to
+ *   R12 Algorithm 1's repair, an option used by the sweeps (Section 4.1 leaves it to
  *       "mission swaps" of Algorithm 2 and a retry): when no vehicle can take mission m
  *       and some mission is already placed, one sweep of Algorithm 2 (readings S1-S3)
  *       runs over the partial schedule, and m is tried once more if the sweep moved
@@ -465,7 +465,7 @@ static int greedy_pick(const orc_instance *in, const sched *s, sched *t, int m) 
   return best_v;
 }
 
-/* Algorithm 1 (reading R8, and R9 when `repair` is set). */
+/* Algorithm 1 (reading R8, and R12 when `repair` is set). */
 static int greedy_core(const orc_instance *in, int repair, int32_t *off_out, int32_t *route_out) {
   int rc = check_instance(in);
   if (rc != ORC_OK) return rc;
@@ -493,7 +493,7 @@ static int greedy_core(const orc_instance *in, int repair, int32_t *off_out, int
     int m = order[k];
     int v = greedy_pick(in, &s, &t, m);
     if (v < 0 && repair && k > 0) {
-      /* R9: one sweep of Algorithm 2 over the partial schedule, then one more try. */
+      /* R12: one sweep of Algorithm 2 over the partial schedule, then one more try. */
       sweep_ctx c = {0};
       c.best_step = -1;
       c.z = c.z_best = sched_cost(in, &s, NULL, NULL);
@@ -516,7 +516,7 @@ int32_t orc_greedy_init(const orc_instance *in, int32_t *off_out, int32_t *route
   return greedy_core(in, 0, off_out, route_out);
 }
 
-/* Algorithm 1 with the repair of R9. */
+/* Algorithm 1 with the repair of R12. */
 int32_t orc_greedy_init_repair(const orc_instance *in, int32_t *off_out, int32_t *route_out) {
   return greedy_core(in, 1, off_out, route_out);
 }
@@ -742,7 +742,7 @@ static int sweep_search(const orc_instance *in, int use_tabu, int accept_worse, 
   return rc;
 }
 
-/* Algorithm 2 (readings S1-S3, S5), started from Algorithm 1 (with the repair of R9
+/* Algorithm 2 (readings S1-S3, S5), started from Algorithm 1 (with the repair of R12
  * when `repair` is set) unless init_off / init_route give the start.
  * z_out[3] = {best, initial, final} objectives;
  * counts_out[4] = {sweeps, moves applied, steps, step of the best (-1: initial)}. */

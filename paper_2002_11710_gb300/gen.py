@@ -195,23 +195,25 @@ def make_instance(seed: int, *, n_bases: int, n_vehicles: int, n_facilities: int
     if deadlines and not deadline_window:
         dl = rng.integers(deadline_lo, horizon + 1, size=n_missions).astype(np.int32)
     elif deadlines:
-        dl = np.zeros(n_missions, dtype=np.int32)
+        # windows [lo, hi] per (mission, vehicle): leave base at 0, arrive by w, home by the horizon
         pk, dv = p + n_bases, d + n_bases
-        for j in range(n_missions):
-            wins = []
-            for v in range(n_vehicles):
-                if heli is not None and heli[j] and veh_type[v] != 0:
-                    continue
-                T = travel[veh_type[v]]
-                b = veh_base[v]
-                lo = max(deadline_lo, int(T[b, pk[j]]) + int(T[pk[j], dv[j]]))
-                hi = horizon - int(T[dv[j], b])
-                if lo <= hi:
-                    wins.append((lo, hi))
-            if not wins:
-                raise ValueError(f"mission {j} fits no vehicle within the horizon")
-            lo, hi = wins[int(rng.integers(len(wins)))]
-            dl[j] = int(rng.integers(lo, hi + 1))
+        T = travel[veh_type]  # [V][L][L], each vehicle's own layer
+        vi = np.arange(n_vehicles)[None, :]
+        lo = np.maximum(deadline_lo, T[vi, veh_base[None, :], pk[:, None]] + T[vi, pk[:, None], dv[:, None]])
+        hi = horizon - T[vi, dv[:, None], veh_base[None, :]]
+        ok = lo <= hi
+        if heli is not None:
+            ok &= ~((heli[:, None] != 0) & (veh_type[None, :] != 0))
+        n_ok = ok.sum(axis=1)
+        if (n_ok == 0).any():
+            raise ValueError(f"mission {int(np.argmin(n_ok))} fits no vehicle within the horizon")
+        # one vehicle window per mission (uniform over the valid ones), then w uniform in it
+        pick = np.minimum((rng.random(n_missions) * n_ok).astype(np.int64), n_ok - 1)
+        col = np.argmax(np.cumsum(ok, axis=1) > pick[:, None], axis=1)
+        rows = np.arange(n_missions)
+        lo_j, hi_j = lo[rows, col], hi[rows, col]
+        dl = (lo_j + np.minimum((rng.random(n_missions) * (hi_j - lo_j + 1)).astype(np.int64),
+                                hi_j - lo_j)).astype(np.int32)
     return Instance(
         travel=travel,
         veh_base=veh_base,

@@ -167,7 +167,7 @@ def _rederive(inst, mode, lam, routes, is_tabu, tenure, accept_worse, max_sweeps
 
 
 def _greedy(inst, mode, lam, repair):
-    """Algorithm 1 (R8, and the repair of R9) re-derived on explicit partial schedules."""
+    """Algorithm 1 (R8, and the repair of R12) re-derived on explicit partial schedules."""
     M, V = inst.n_missions, inst.n_vehicles
     heli = inst.heli_only
     dl = inst.deadline
@@ -312,13 +312,13 @@ def test_sweep_reports_infeasible_start():
     assert oracle.tabu_sweep(pb, 3, 5)["status"] == oracle.E_INFEASIBLE_INIT
 
 
-REPAIR_CASES = [(23, 14, ilp.HARD), (60, 14, ilp.HARD), (72, 18, ilp.HARD), (57, 22, ilp.HARD),
-                (34, 26, ilp.HARD), (96, 30, ilp.PENALTY), (116, 30, ilp.PENALTY)]
+REPAIR_CASES = [(235, 18, ilp.HARD), (23, 22, ilp.HARD), (162, 22, ilp.HARD), (3, 26, ilp.HARD),
+                (13, 30, ilp.HARD), (75, 30, ilp.PENALTY), (110, 30, ilp.PENALTY)]
 
 
 @pytest.mark.parametrize("case", REPAIR_CASES)
 def test_greedy_repair_rederived(case):
-    """Paper-fleet instances where Algorithm 1 gets stuck and the repair sweep (R9)
+    """Paper-fleet instances where Algorithm 1 gets stuck and the repair sweep (R12)
     frees a place: the oracle's start equals the re-derived one."""
     seed, m, mode = case
     inst = gen.paper_fleet(seed, m)
