@@ -403,6 +403,56 @@ def run_serving(args, dev):
                                                  "p99": float(np.percentile(lat2, 99) * 1e3)}}}
 
 
+def run_travel_matrix(args, bp, insts, dev):
+    """Row f4: every instance's [2][L][L] matrix rebuilt on the device from coordinates
+    (asched_travel_matrix) into the batch's travel array, Euclidean on the km coordinates
+    and Haversine (Eq. e1) on the same points mapped into a 14 x 21 degree box; checked
+    against the host-built matrices (Euclidean: bit for bit). Roofline: the algorithmic
+    bytes are the int32 matrix entries written (plus 16 B of coordinates per location)."""
+    import torch
+
+    from paper_2002_11710_gb300 import api
+
+    xy = np.concatenate([i.coords for i in insts])
+    coords = torch.from_numpy(xy).to(dev, torch.float64)
+    ll = torch.from_numpy(np.stack([42.0 + xy[:, 1] / 1000.0 * 14.0, -95.0 + xy[:, 0] / 1000.0 * 21.0],
+                                   axis=1)).to(dev, torch.float64)
+    want = bp.travel.clone()
+    hbm = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm = float(json.load(f).get("hbm_gbs"))
+    except (OSError, TypeError, ValueError):
+        pass
+    L = np.diff(bp.h_loc_off).astype(np.int64)
+    pairs = int((L * L).sum())
+    nbytes = 4 * bp.n_types * pairs + 16 * int(L.sum())
+    res = {"workload": f"{bp.B:,} instances, {pairs:,} location pairs, 2 layers (300 / 500 km/h)",
+           "bytes_per_launch": nbytes, "gpu_launches": 1}
+    for name, c, metric in (("euclidean", coords, api.METRIC_EUCLIDEAN), ("haversine", ll, api.METRIC_HAVERSINE)):
+        for _ in range(2):
+            st = api.travel_into_batch(bp, c, [300.0, 500.0], metric)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(5):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            api.travel_into_batch(bp, c, [300.0, 500.0], metric)
+            b.record()
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        t = statistics.median(ms)
+        res[name] = {"ms": t, "GB_per_s": nbytes / t / 1e6, "pairs_per_s": pairs / t * 1e3,
+                     "status": int(st.item())}
+        if hbm:
+            res[name]["frac_of_measured_hbm"] = nbytes / t / 1e6 / hbm
+        if metric == api.METRIC_EUCLIDEAN:
+            res[name]["equals_host_matrices"] = bool(torch.equal(bp.travel, want))
+    bp.travel.copy_(want)
+    return res
+
+
 def run_sweeps(args, dev):
     """The paper's own local searches (Algorithm 2, Neighbourhood Search; Algorithm 3 as
     printed, the per-mission sweep) started from Algorithm 1 with its repair, by default on
@@ -425,6 +475,7 @@ def run_sweeps(args, dev):
                         "M ~ U[12, 33], 12 vehicles (4 planes), HARD 600 min cap, arrive-by windows, "
                         "Algorithm 1 with repair, at most 100 sweeps, tenure 7"),
            "gpu_launches": 1}
+    out["travel_matrix"] = run_travel_matrix(args, bp, insts, dev)
     for name, alg in (("algorithm_2", api.SWEEP_NEIGHBOURHOOD), ("algorithm_3", api.SWEEP_TABU)):
         params = api.sweep_params(100, api.HARD, 1000, 7, repair=True)
         res, _ = api.sweep_batch(bp, alg, params)

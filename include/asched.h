@@ -423,6 +423,39 @@ typedef struct {
 int asched_sweep_batch(const asched_batch* batch, int32_t algorithm, const asched_params* params,
                        const asched_batch_result* out, const asched_sweep_trace* trace, void* stream);
 
+/* ---------------------------------------------------------------- travel matrix ----
+ * Travel-time matrices built on the device from location coordinates (Eq. e1,
+ * Section 3), written straight into the concatenated travel array of an asched_batch:
+ *   travel[travel_off[b] + (t * L_b + i) * L_b + j] = rint(dist_km(i, j) / speed_kmh[t] * 60)
+ * in float64, half to even, where L_b = loc_off[b + 1] - loc_off[b] and dist_km is
+ *   ASCHED_METRIC_HAVERSINE  Eq. e1's great-circle distance, 2 r asin(sqrt(sin^2(dphi/2)
+ *                            + cos(phi_i) cos(phi_j) sin^2(dpsi/2))), sqrt clipped to 1;
+ *                            coords are (latitude, longitude) in degrees;
+ *   ASCHED_METRIC_EUCLIDEAN  sqrt(dx^2 + dy^2) on (x, y) kilometres, every operation
+ *                            rounded separately (identical to a float64 evaluation).
+ * The Haversine path uses the device's sine, cosine and arcsine: a time within a few
+ * ulps of a half minute may round the other way than on a host. */
+#define ASCHED_METRIC_EUCLIDEAN 0
+#define ASCHED_METRIC_HAVERSINE 1
+
+typedef struct {
+  int32_t n_instances;
+  const int32_t* h_loc_off;  /* HOST [n_instances + 1], h_loc_off[0] = 0, every L_b >= 1 */
+  const int32_t* loc_off;    /* device copy of h_loc_off */
+  const int64_t* travel_off; /* device [n_instances]: start of instance b's block */
+  const double* coords;      /* device [h_loc_off[B]][2] */
+  int32_t n_types;           /* 1 or 2 */
+  double speed_kmh[2];       /* per vehicle type, > 0 (the paper: 300 helicopter, 500 plane) */
+  int32_t metric;            /* ASCHED_METRIC_* */
+  double radius_km;          /* Haversine only; 0 = 6371 */
+} asched_travel_spec;
+
+/* Queue the matrices of every instance on `stream`. travel: device, laid out as
+ * asched_batch.travel. status: device int32 or NULL; the call sets it to ASCHED_OK, and
+ * the kernel to ASCHED_E_INVALID if a coordinate is not finite or a time does not fit
+ * int32 (such entries are written as 0). */
+int asched_travel_matrix(const asched_travel_spec* spec, int32_t* travel, int32_t* status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

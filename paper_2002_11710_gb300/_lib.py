@@ -90,6 +90,15 @@ class SweepTrace(ctypes.Structure):
     _fields_ = [("move", P), ("z", P), ("capacity", ctypes.c_int32)]
 
 
+class TravelSpec(ctypes.Structure):
+    _fields_ = [("n_instances", ctypes.c_int32), ("h_loc_off", P), ("loc_off", P),
+                ("travel_off", P), ("coords", P), ("n_types", ctypes.c_int32),
+                ("speed_kmh", ctypes.c_double * 2), ("metric", ctypes.c_int32),
+                ("radius_km", ctypes.c_double)]
+
+
+METRIC_EUCLIDEAN, METRIC_HAVERSINE = 0, 1
+
 SWEEP_NEIGHBOURHOOD = 2  # Algorithm 2
 SWEEP_TABU = 3  # Algorithm 3 as printed
 SWEEP_ACCEPT_WORSE = 4  # asched_params.flags bits for the sweeps
@@ -114,6 +123,7 @@ SIGNATURES = {
                                            ctypes.c_int32, P, P]),
     "asched_serve": (ctypes.c_int, [P, P, ctypes.c_int64, ctypes.c_int32, P]),
     "asched_sweep_batch": (ctypes.c_int, [P, ctypes.c_int32, P, P, P, P]),
+    "asched_travel_matrix": (ctypes.c_int, [P, P, P, P]),
 }
 
 _lock = threading.Lock()

@@ -448,3 +448,54 @@ def sweep_batch(bp: BatchProblem, algorithm: int, params: _lib.Params, out: Opti
                                         ctypes.c_void_p(s.cuda_stream))
     _lib.check(rc, "asched_sweep_batch")
     return out, trace
+
+
+METRIC_EUCLIDEAN, METRIC_HAVERSINE = _lib.METRIC_EUCLIDEAN, _lib.METRIC_HAVERSINE
+
+
+def travel_into_batch(bp: BatchProblem, coords: torch.Tensor, speeds_kmh, metric: int = METRIC_EUCLIDEAN,
+                      radius_km: float = 0.0, stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+    """Queue asched_travel_matrix: rebuild every instance's travel matrix in bp.travel from
+    coords (device float64 [total locations, 2], instance b's rows at bp.h_loc_off[b]).
+    Returns the device status word (ASCHED_OK, or E_INVALID for a non-finite coordinate
+    or a time beyond int32)."""
+    if coords.dtype != torch.float64 or tuple(coords.shape) != (int(bp.h_loc_off[-1]), 2):
+        raise ValueError("coords must be a float64 [total locations, 2] tensor")
+    coords = coords.to(bp.device).contiguous()
+    sp = [float(x) for x in speeds_kmh]
+    if len(sp) != bp.n_types:
+        raise ValueError("one speed per travel layer")
+    status = torch.zeros(1, dtype=torch.int32, device=bp.device)
+    hp = ctypes.c_void_p(bp.h_loc_off.ctypes.data)
+    spec = _lib.TravelSpec(bp.B, hp, _ptr(bp.loc_off), _ptr(bp.travel_off), _ptr(coords), bp.n_types,
+                           (ctypes.c_double * 2)(*(sp + [1.0])[:2]), int(metric), float(radius_km))
+    s = stream if stream is not None else torch.cuda.current_stream(bp.device)
+    rc = _lib.load().asched_travel_matrix(ctypes.byref(spec), _ptr(bp.travel), _ptr(status),
+                                          ctypes.c_void_p(s.cuda_stream))
+    _lib.check(rc, "asched_travel_matrix")
+    bp._keep_coords = coords  # the launch reads it until the stream gets there
+    return status
+
+
+def travel_matrix(coords, speeds_kmh, metric: int = METRIC_EUCLIDEAN, radius_km: float = 0.0,
+                  device="cuda") -> torch.Tensor:
+    """One instance's [n_types, L, L] int32 travel minutes built on the device from
+    coords [L, 2] (see asched_travel_matrix)."""
+    c = torch.as_tensor(np.ascontiguousarray(coords, dtype=np.float64)).to(device)
+    L, nt = int(c.shape[0]), len(speeds_kmh)
+    dev = torch.device(device)
+    h_loc = np.array([0, L], dtype=np.int32)
+    loc = torch.from_numpy(h_loc).to(dev)
+    toff = torch.zeros(1, dtype=torch.int64, device=dev)
+    out = torch.empty((nt, L, L), dtype=torch.int32, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    sp = [float(x) for x in speeds_kmh]
+    spec = _lib.TravelSpec(1, ctypes.c_void_p(h_loc.ctypes.data), _ptr(loc), _ptr(toff), _ptr(c), nt,
+                           (ctypes.c_double * 2)(*(sp + [1.0])[:2]), int(metric), float(radius_km))
+    s = torch.cuda.current_stream(dev)
+    _lib.check(_lib.load().asched_travel_matrix(ctypes.byref(spec), _ptr(out), _ptr(status),
+                                                ctypes.c_void_p(s.cuda_stream)), "asched_travel_matrix")
+    s.synchronize()
+    if int(status.item()) != OK:
+        raise AschedError(int(status.item()), "asched_travel_matrix (device)")
+    return out

@@ -47,6 +47,8 @@ class Instance:
     deadline   [M] arrive-by minute at the delivery, or None (no deadlines)
     duty_cap   maximum flight minutes per vehicle (the constant p)
     horizon    latest return-to-base minute when deadlines are on (24 h)
+    coords     [L, 2] float64 location coordinates the matrix was built from (x, y km),
+               or None
     """
 
     travel: np.ndarray
@@ -59,6 +61,7 @@ class Instance:
     duty_cap: int
     horizon: int = 1440
     name: str = ""
+    coords: Optional[np.ndarray] = None
 
     @property
     def n_loc(self) -> int:
@@ -225,6 +228,7 @@ def make_instance(seed: int, *, n_bases: int, n_vehicles: int, n_facilities: int
         duty_cap=int(duty_cap),
         horizon=int(horizon),
         name=name,
+        coords=np.ascontiguousarray(xy, dtype=np.float64),
     )
 
 

@@ -1,0 +1,137 @@
+"""asched_travel_matrix (Eq. e1 on the device) against the oracle's definition, and the
+whole path coordinates -> matrices -> search (needs a GB300)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import travel
+from paper_2002_11710_gb300 import api, gen
+
+pytestmark = pytest.mark.gpu
+
+
+def _coords_tensor(insts):
+    return torch.from_numpy(np.concatenate([i.coords for i in insts])).to("cuda", torch.float64)
+
+
+def test_euclidean_bit_exact_on_the_workloads():
+    """Every batched-workload member's matrix rebuilt on the device from its coordinates
+    equals the oracle's (and so the generator's) integers exactly."""
+    insts = [gen.batched_member(i) for i in range(1024)]
+    bp = api.BatchProblem(insts)
+    want = bp.travel.clone()
+    bp.travel.zero_()
+    status = api.travel_into_batch(bp, _coords_tensor(insts), [250.0])
+    torch.cuda.synchronize()
+    assert int(status.item()) == api.OK
+    assert torch.equal(bp.travel, want)
+    for b in (0, 17, 1023):
+        o = travel.travel_minutes(insts[b].coords, [250.0], travel.EUCLIDEAN)
+        t0 = int(bp.h_travel_off[b])
+        L = insts[b].n_loc
+        np.testing.assert_array_equal(bp.travel[t0:t0 + L * L].cpu().numpy().reshape(1, L, L), o)
+
+
+def test_euclidean_two_layers_and_ragged_sizes():
+    rng = np.random.default_rng(2)
+    sizes = [1, 2, 31, 32, 33, 64, 95, 300]
+    coords = [rng.uniform(-500.0, 2500.0, size=(L, 2)) for L in sizes]
+    insts = []
+    for c in coords:
+        L = len(c)
+        inst = gen.random_instance(1, n_loc=max(L, 2), n_vehicles=1, n_missions=0, n_types=2)
+        inst.travel = np.zeros((2, L, L), np.int32)
+        inst.veh_base = np.zeros(1, np.int32)
+        inst.coords = c
+        insts.append(inst)
+    bp = api.BatchProblem(insts)
+    status = api.travel_into_batch(bp, _coords_tensor(insts), [300.0, 500.0])
+    torch.cuda.synchronize()
+    assert int(status.item()) == api.OK
+    for b, c in enumerate(coords):
+        L = len(c)
+        t0 = int(bp.h_travel_off[b])
+        got = bp.travel[t0:t0 + 2 * L * L].cpu().numpy().reshape(2, L, L)
+        np.testing.assert_array_equal(got, travel.travel_minutes(c, [300.0, 500.0], travel.EUCLIDEAN))
+
+
+@pytest.mark.parametrize("region", ["ontario", "globe"])
+def test_haversine_matches_the_oracle(region):
+    """Exact wherever the oracle's unrounded time is not within 1e-6 minutes of a half
+    minute (device and host trigonometry may differ in the last bits), else within 1."""
+    rng = np.random.default_rng(4)
+    if region == "ontario":  # the paper's setting: bases and hospitals in one province
+        ll = np.stack([rng.uniform(42.0, 56.0, 400), rng.uniform(-95.0, -74.0, 400)], axis=1)
+    else:
+        ll = np.stack([rng.uniform(-89.0, 89.0, 400), rng.uniform(-180.0, 180.0, 400)], axis=1)
+    got = api.travel_matrix(ll, [300.0, 500.0], api.METRIC_HAVERSINE).cpu().numpy()
+    want = travel.travel_minutes(ll, [300.0, 500.0], travel.HAVERSINE)
+    raw = travel.minutes_unrounded(ll, [300.0, 500.0], travel.HAVERSINE)
+    near_half = np.abs(np.abs(raw - np.floor(raw)) - 0.5) < 1e-6
+    assert np.array_equal(got[~near_half], want[~near_half])
+    assert np.abs(got.astype(np.int64) - want).max() <= 1
+    assert (got == np.transpose(got, (0, 2, 1))).all()
+    assert (np.diagonal(got, axis1=1, axis2=2) == 0).all()
+
+
+def test_status_and_host_errors():
+    ll = np.array([[0.0, 0.0], [np.nan, 1.0], [1.0, 1.0]])
+    with pytest.raises(api.AschedError) as e:
+        api.travel_matrix(ll, [300.0], api.METRIC_HAVERSINE)
+    assert e.value.status == api.E_INVALID
+    big = np.array([[0.0, 0.0], [1e12, 0.0]])  # 6e10 minutes at 1 km/h does not fit int32
+    with pytest.raises(api.AschedError):
+        api.travel_matrix(big, [1.0], api.METRIC_EUCLIDEAN)
+    for speeds, metric in (([0.0], api.METRIC_EUCLIDEAN), ([300.0], 7), ([1.0, 2.0, 3.0], 0)):
+        with pytest.raises((api.AschedError, ValueError)):
+            api.travel_matrix([[0.0, 0.0], [1.0, 1.0]], speeds, metric)
+
+
+def test_coordinates_to_schedules_end_to_end():
+    """Matrices built on the device feed the batched search and the sweeps directly; the
+    results equal those from the host-built matrices."""
+    insts = [gen.paper_fleet(s, 12 + s % 22) for s in range(64)]
+    bp_host = api.BatchProblem(insts)
+    bp_dev = api.BatchProblem(insts)
+    bp_dev.travel.zero_()
+    status = api.travel_into_batch(bp_dev, _coords_tensor(insts), [300.0, 500.0])
+    params = api.make_params(7, 200, api.PENALTY, 1000)
+    a = api.solve_batch(bp_host, params)
+    b = api.solve_batch(bp_dev, params)
+    sp = api.sweep_params(50, api.HARD, 1000, 7, repair=True)
+    c, _ = api.sweep_batch(bp_host, api.SWEEP_TABU, sp)
+    d, _ = api.sweep_batch(bp_dev, api.SWEEP_TABU, sp)
+    torch.cuda.synchronize()
+    assert int(status.item()) == api.OK
+    assert torch.equal(bp_host.travel, bp_dev.travel)
+    for x, y in ((a, b), (c, d)):
+        assert torch.equal(x.info, y.info) and torch.equal(x.route, y.route)
+
+
+def test_half_minute_boundaries_go_through_float64():
+    """Points whose times sit exactly on, or a hair off, half minutes: the float32 screen
+    must hand them to float64, and the integers equal the oracle's exactly."""
+    xs = [0.0]
+    for k in range(1, 60):
+        for eps in (0.0, 1e-12, -1e-12, 1e-9, -1e-9, 1e-6, -1e-6, 3e-5, -3e-5):
+            for speed in (60.0, 300.0, 500.0):
+                xs.append((k + 0.5) * speed / 60.0 + eps)
+    xy = np.stack([np.array(xs), np.zeros(len(xs))], axis=1)
+    for speeds in ([60.0, 300.0], [500.0]):
+        got = api.travel_matrix(xy, speeds, api.METRIC_EUCLIDEAN).cpu().numpy()
+        np.testing.assert_array_equal(got, travel.travel_minutes(xy, speeds, travel.EUCLIDEAN))
+
+
+def test_haversine_near_antipodes_and_tiny_distances():
+    rng = np.random.default_rng(9)
+    lat = rng.uniform(-60, 60, 100)
+    lon = rng.uniform(-180, 180, 100)
+    anti = np.stack([-lat + rng.normal(0, 0.5, 100), lon + 180.0 + rng.normal(0, 0.5, 100)], axis=1)
+    near = np.stack([lat + rng.normal(0, 1e-4, 100), lon + rng.normal(0, 1e-4, 100)], axis=1)
+    ll = np.concatenate([np.stack([lat, lon], axis=1), anti, near])
+    got = api.travel_matrix(ll, [300.0, 500.0], api.METRIC_HAVERSINE).cpu().numpy()
+    want = travel.travel_minutes(ll, [300.0, 500.0], travel.HAVERSINE)
+    raw = travel.minutes_unrounded(ll, [300.0, 500.0], travel.HAVERSINE)
+    near_half = np.abs(np.abs(raw - np.floor(raw)) - 0.5) < 1e-6
+    assert np.array_equal(got[~near_half], want[~near_half])
+    assert np.abs(got.astype(np.int64) - want).max() <= 1
