@@ -15,21 +15,25 @@
 // the integer: rint changes value only at half minutes, so when the float32 time lies
 // farther from the nearest half minute than a bound on its error, it rounds to the same
 // integer as the float64 expression (whose own error is far smaller).
-// Each coordinate is staged as a pair of floats hi + lo (hi = float(v), lo = float(v -
-// hi)), so a difference (hi_i - hi_j) + (lo_i - lo_j) is within 2 * 2^-24 of the exact
-// difference relative to it, plus 2^-47 of the magnitudes. Bounds on the float32 time t:
-//   Euclidean  differences, squares, sum, correctly rounded square root and the product
-//              with a rounded 60 / speed: below 6 * 2^-24 relative; screened at
-//              2e-6 t + (60 / speed) 2^-40 (|x_i| + |x_j| + |y_i| + |y_j|) + 1e-6;
-//   Haversine  half-angle differences, sinf (2 ulp), squares, cos(phi) staged from float64,
-//              sum, square root and asinf (2 ulp) with its condition number below 1.9 for
-//              sqrt(a) <= 0.9 (larger values go to float64 outright): below 1.8e-6
-//              relative; screened at 8e-6 t + (60 / speed) 2 r 2^-40 (sum of |angles|)
-//              + 1e-5.
+// Bounds on the float32 time t (every float32 value of a coordinate is off by at most
+// 2^-24 of its magnitude):
+//   Euclidean  coordinates staged as float32; the differences add at most 2^-24 of the
+//              sum of the four magnitudes, then differences, squares, sum, correctly
+//              rounded square root and the product with a rounded 60 / speed add below
+//              6 * 2^-24 relative; screened at 2e-6 t + (60 / speed) 2^-20 S + 1e-6, S the
+//              instance's largest |x| + |y|;
+//   Haversine  angles staged as float pairs hi + lo (lo = float(v - hi)), so a difference
+//              (hi_i - hi_j) + (lo_i - lo_j) is within 2 * 2^-24 of itself plus 2^-47 of
+//              the magnitudes; half-angle differences, sinf (2 ulp), squares, cos(phi)
+//              staged from float64, sum, square root and asinf (2 ulp) with its condition
+//              number below 1.9 for sqrt(a) <= 0.9 (larger values go to float64 outright)
+//              add below 1.8e-6 relative; screened at 8e-6 t + (60 / speed) 2 r 2^-40
+//              (sum of |angles|) + 1e-5.
 // Times of 2^22 minutes or more also go to float64. The float64 path is the expression
-// above, on the original float64 coordinates. Lanes that need it queue (column, type)
-// in shared memory and the whole warp drains the queue at the end of each row, so the
-// float64 work follows the number of such entries, not the number of warps that meet one.
+// above, on the original float64 coordinates. Lanes that need it queue (row, column,
+// type) in shared memory, and the whole warp drains its queue when it fills and at the
+// end of the instance, so float64 work runs on full warps and follows the number of such
+// entries.
 //
 // One CTA per instance (grid-stride over instances): the instance's coordinates are
 // staged once in shared memory (angles in radians and cos(phi) for Haversine); warps
@@ -97,13 +101,26 @@ __device__ __forceinline__ float diff(const float* h, const float* l, int i, int
   return __fadd_rn(__fsub_rn(h[i], h[j]), __fsub_rn(l[i], l[j]));
 }
 
+// Drain a warp's queue of deferred entries: each lane takes entries and writes the
+// float64 result.
+__device__ __forceinline__ void drain(const MParams& P, const double* c, int32_t* base, int L, int64_t LL,
+                                      const int* q, int n, int lane, int& bad) {
+  __syncwarp();
+  for (int k = lane; k < n; k += 32) {
+    const int e = q[k];
+    const int i = e >> 12, j = (e >> 1) & 2047, t = e & 1;
+    base[t * LL + static_cast<int64_t>(i) * L + j] = checked(minutes64(P, c, i, j, t), bad);
+  }
+  __syncwarp();
+}
+
+template <bool HAV>
 __global__ void __launch_bounds__(kWarps * 32) travel_kernel(const __grid_constant__ MParams P) {
   __shared__ Stage st;
   __shared__ int queue[kWarps][kQueue];
+  __shared__ unsigned s_mag;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool hav = P.metric == ASCHED_METRIC_HAVERSINE;
   const float two_r32 = static_cast<float>(P.two_r);
-  const float tiny = 9.094947e-13f;  // 2^-40
   int bad = 0;
   for (int b = blockIdx.x; b < P.B; b += gridDim.x) {
     const int lo = P.loc_off[b];
@@ -118,34 +135,39 @@ __global__ void __launch_bounds__(kWarps * 32) travel_kernel(const __grid_consta
       continue;
     }
     __syncthreads();  // the previous instance's stage is no longer read
+    if (threadIdx.x == 0) s_mag = 0u;
+    __syncthreads();
     for (int l = threadIdx.x; l < L; l += blockDim.x) {
       double x = c[2 * l], y = c[2 * l + 1];
-      if (hav) {
+      const float xh = static_cast<float>(HAV ? x * P.deg : x), yh = static_cast<float>(HAV ? y * P.deg : y);
+      st.xh[l] = xh;
+      st.yh[l] = yh;
+      if (HAV) {
         x *= P.deg;
         y *= P.deg;
         st.cphi[l] = static_cast<float>(cos(x));
+        st.xl[l] = static_cast<float>(x - static_cast<double>(xh));
+        st.yl[l] = static_cast<float>(y - static_cast<double>(yh));
+      } else {
+        const float m = fabsf(xh) + fabsf(yh);  // >= 0 (or NaN, whose bits exceed every finite value)
+        atomicMax(&s_mag, __float_as_uint(m));
       }
-      const float xh = static_cast<float>(x), yh = static_cast<float>(y);
-      st.xh[l] = xh;
-      st.xl[l] = static_cast<float>(x - static_cast<double>(xh));
-      st.yh[l] = yh;
-      st.yl[l] = static_cast<float>(y - static_cast<double>(yh));
     }
     __syncthreads();
+    const float S = __uint_as_float(s_mag);
     int* q = queue[warp];
+    int n = 0;  // queued entries (warp-uniform)
     for (int i = warp; i < L; i += kWarps) {
       int32_t* row = base + static_cast<int64_t>(i) * L;
-      int n = 0;  // queued entries of this row (warp-uniform)
       for (int j0 = 0; j0 < L; j0 += 32) {
         const int j = j0 + lane;
         const bool live = j < L;
         const int jj = live ? j : i;
-        const float dx = diff(st.xh, st.xl, i, jj), dy = diff(st.yh, st.yl, i, jj);
-        float d32, rel, abs_part;
+        float d32, rel, abs_part, magk;
         bool screen = true;
-        const float mag = tiny * (fabsf(st.xh[i]) + fabsf(st.xh[jj]) + fabsf(st.yh[i]) + fabsf(st.yh[jj]));
-        float magk;
-        if (hav) {
+        if (HAV) {
+          const float dx = __fadd_rn(__fsub_rn(st.xh[i], st.xh[jj]), __fsub_rn(st.xl[i], st.xl[jj]));
+          const float dy = __fadd_rn(__fsub_rn(st.yh[i], st.yh[jj]), __fsub_rn(st.yl[i], st.yl[jj]));
           const float s1 = sinf(__fmul_rn(dx, 0.5f)), s2 = sinf(__fmul_rn(dy, 0.5f));
           const float a = __fadd_rn(__fmul_rn(s1, s1), __fmul_rn(__fmul_rn(st.cphi[i], st.cphi[jj]), __fmul_rn(s2, s2)));
           const float r = __fsqrt_rn(a);
@@ -153,12 +175,14 @@ __global__ void __launch_bounds__(kWarps * 32) travel_kernel(const __grid_consta
           d32 = __fmul_rn(two_r32, asinf(r));
           rel = 8e-6f;
           abs_part = 1e-5f;
-          magk = two_r32 * mag;
+          magk = two_r32 * 9.094947e-13f *  // 2 r 2^-40 (sum of |angles|)
+                 (fabsf(st.xh[i]) + fabsf(st.xh[jj]) + fabsf(st.yh[i]) + fabsf(st.yh[jj]));
         } else {
+          const float dx = __fsub_rn(st.xh[i], st.xh[jj]), dy = __fsub_rn(st.yh[i], st.yh[jj]);
           d32 = __fsqrt_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)));
           rel = 2e-6f;
           abs_part = 1e-6f;
-          magk = mag;
+          magk = 9.536743e-7f * S;  // 2^-20 S
         }
         for (int t = 0; t < P.nt; ++t) {
           const float t32 = __fmul_rn(d32, P.k32[t]);
@@ -168,27 +192,17 @@ __global__ void __launch_bounds__(kWarps * 32) travel_kernel(const __grid_consta
           if (live && sure) row[t * LL + j] = static_cast<int32_t>(rintf(t32));
           const unsigned need = __ballot_sync(0xffffffffu, live && !sure);
           if (need) {
-            if (n + 32 > kQueue) {  // drain a full queue first
-              __syncwarp();
-              for (int k = lane; k < n; k += 32) {
-                const int e = q[k];
-                row[(e & 1) * LL + (e >> 1)] = checked(minutes64(P, c, i, e >> 1, e & 1), bad);
-              }
-              __syncwarp();
+            if (n + 32 > kQueue) {
+              drain(P, c, base, L, LL, q, n, lane, bad);
               n = 0;
             }
-            if (live && !sure) q[n + __popc(need & ((1u << lane) - 1u))] = (j << 1) | t;
+            if (live && !sure) q[n + __popc(need & ((1u << lane) - 1u))] = (i << 12) | (j << 1) | t;
             n += __popc(need);
           }
         }
       }
-      __syncwarp();
-      for (int k = lane; k < n; k += 32) {
-        const int e = q[k];
-        row[(e & 1) * LL + (e >> 1)] = checked(minutes64(P, c, i, e >> 1, e & 1), bad);
-      }
-      __syncwarp();
     }
+    drain(P, c, base, L, LL, q, n, lane, bad);
   }
   if (bad && P.status) atomicExch(P.status, ASCHED_E_INVALID);
 }
@@ -238,7 +252,10 @@ extern "C" int asched_travel_matrix(const asched_travel_spec* spec, int32_t* tra
   }
   const int64_t cap = static_cast<int64_t>(sms) * 4;  // up to 4 CTAs of 256 threads per SM
   const int grid = static_cast<int>(B < cap ? B : cap);
-  travel_kernel<<<grid, kWarps * 32, 0, st>>>(q);
+  if (q.metric == ASCHED_METRIC_HAVERSINE)
+    travel_kernel<true><<<grid, kWarps * 32, 0, st>>>(q);
+  else
+    travel_kernel<false><<<grid, kWarps * 32, 0, st>>>(q);
   if (cudaGetLastError() != cudaSuccess) return ASCHED_E_CUDA;
   return ASCHED_OK;
 }
