@@ -88,10 +88,10 @@ def lib():
             L.orc_greedy_init_repair.restype = ctypes.c_int32
             L.orc_greedy_init_repair.argtypes = [P, P, P]
             L.orc_neighbourhood_search.argtypes = [P, ctypes.c_int32, ctypes.c_int32, P, P, P, P, P,
-                                                   P, P, P, ctypes.c_int64]
+                                                   P, P, P, P, P, ctypes.c_int64]
             L.orc_tabu_sweep.restype = ctypes.c_int32
             L.orc_tabu_sweep.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
-                                         ctypes.c_int32, P, P, P, P, P, P, P, P, ctypes.c_int64]
+                                         ctypes.c_int32, P, P, P, P, P, P, P, P, P, P, ctypes.c_int64]
             _lib = L
     return _lib
 
@@ -203,7 +203,7 @@ def tabu_search(pb: Problem, tenure: int, iterations: int, init=None):
             "traj_z": traj_z[:iterations]}
 
 
-def _sweep(pb: Problem, fn, args, init, trace_cap):
+def _sweep(pb: Problem, fn, args, init, trace_cap, vorder, mrank):
     off = np.zeros(pb.V + 1, dtype=np.int32)
     route = np.zeros(max(pb.M, 1), dtype=np.int32)
     moves = np.zeros(max(trace_cap, 1), dtype=np.uint32)
@@ -216,8 +216,10 @@ def _sweep(pb: Problem, fn, args, init, trace_cap):
         ip = (_ptr(ioff), _ptr(iroute))
     else:
         ip = (None, None)
-    rc = fn(pb.ref, *args, ip[0], ip[1], _ptr(off), _ptr(route), _ptr(zo), _ptr(counts),
-            _ptr(moves), _ptr(zs), int(trace_cap))
+    vo = None if vorder is None else np.ascontiguousarray(vorder, dtype=np.int32)
+    mr = None if mrank is None else np.ascontiguousarray(mrank, dtype=np.int32)
+    rc = fn(pb.ref, *args, _ptr(vo), _ptr(mr), ip[0], ip[1], _ptr(off), _ptr(route), _ptr(zo),
+            _ptr(counts), _ptr(moves), _ptr(zs), int(trace_cap))
     n = min(int(counts[2]), trace_cap)
     return {"status": int(rc), "route_off": off, "route": route[:pb.M], "z_best": int(zo[0]),
             "z_init": int(zo[1]), "z_final": int(zo[2]), "sweeps": int(counts[0]),
@@ -226,16 +228,16 @@ def _sweep(pb: Problem, fn, args, init, trace_cap):
 
 
 def neighbourhood_search(pb: Problem, max_sweeps: int, repair: bool = False, init=None,
-                         trace_cap: int = 1 << 16):
+                         trace_cap: int = 1 << 16, vorder=None, mrank=None):
     """Algorithm 2 (readings S1-S3, S5 in the C file) from Algorithm 1 (R8, or R12 with
-    repair). One trace entry per mission step."""
+    repair). One trace entry per mission step. vorder / mrank: the loop orders (S1)."""
     return _sweep(pb, lib().orc_neighbourhood_search, (int(max_sweeps), int(bool(repair))), init,
-                  trace_cap)
+                  trace_cap, vorder, mrank)
 
 
 def tabu_sweep(pb: Problem, tenure: int, max_sweeps: int, accept_worse: bool = False,
-               repair: bool = False, init=None, trace_cap: int = 1 << 16):
+               repair: bool = False, init=None, trace_cap: int = 1 << 16, vorder=None, mrank=None):
     """Algorithm 3 as printed: per-mission sweep with a tabu list (readings S1, S2, S4 or,
     with accept_worse, S4b; S5)."""
     return _sweep(pb, lib().orc_tabu_sweep, (int(tenure), int(max_sweeps), int(bool(accept_worse)),
-                                             int(bool(repair))), init, trace_cap)
+                                             int(bool(repair))), init, trace_cap, vorder, mrank)

@@ -384,6 +384,8 @@ typedef struct {
   uint32_t *trace_move;
   int64_t *trace_z;
   int64_t trace_cap;
+  const int32_t *vorder; /* [V] order of the vehicles' turns, or NULL for 0..V-1 (S1) */
+  const int32_t *mrank;  /* [M] rank of each mission within its vehicle's turn, or NULL (S1) */
 } sweep_ctx;
 
 /* One sweep over s (readings S1, S2 and S3 / S4 / S4b). s may be partial: missions that
@@ -391,9 +393,17 @@ typedef struct {
  * applied. */
 static int sweep_pass(const orc_instance *in, sched *s, sched *t, int32_t *snap, sweep_ctx *c) {
   int M = s->M, V = s->V, applied = 0;
-  for (int i = 0; i < V; i++) {
+  for (int ii = 0; ii < V; ii++) {
+    int i = c->vorder ? c->vorder[ii] : ii;
     int ni = s->len[i];
     memcpy(snap, s->seq + (int64_t)i * M, sizeof(int32_t) * (size_t)ni);
+    if (c->mrank) /* the turn's missions by increasing rank (plain insertion sort) */
+      for (int x = 1; x < ni; x++)
+        for (int y = x; y > 0 && c->mrank[snap[y]] < c->mrank[snap[y - 1]]; y--) {
+          int tmp = snap[y];
+          snap[y] = snap[y - 1];
+          snap[y - 1] = tmp;
+        }
     for (int jj = 0; jj < ni; jj++) {
       int j = snap[jj], vj, kj;
       uint32_t rec = ORC_NULL_MOVE;
@@ -465,8 +475,9 @@ static int greedy_pick(const orc_instance *in, const sched *s, sched *t, int m) 
   return best_v;
 }
 
-/* Algorithm 1 (reading R8, and R12 when `repair` is set). */
-static int greedy_core(const orc_instance *in, int repair, int32_t *off_out, int32_t *route_out) {
+/* Algorithm 1 (reading R8, and R12 when `repair` is set, its sweep in the given orders). */
+static int greedy_core(const orc_instance *in, int repair, const int32_t *vorder, const int32_t *mrank,
+                       int32_t *off_out, int32_t *route_out) {
   int rc = check_instance(in);
   if (rc != ORC_OK) return rc;
   int M = in->n_missions, V = in->n_vehicles;
@@ -497,6 +508,8 @@ static int greedy_core(const orc_instance *in, int repair, int32_t *off_out, int
       sweep_ctx c = {0};
       c.best_step = -1;
       c.z = c.z_best = sched_cost(in, &s, NULL, NULL);
+      c.vorder = vorder;
+      c.mrank = mrank;
       if (sweep_pass(in, &s, &t, snap, &c)) v = greedy_pick(in, &s, &t, m);
     }
     if (v < 0) rc = ORC_E_INFEASIBLE_INIT;
@@ -513,12 +526,12 @@ static int greedy_core(const orc_instance *in, int repair, int32_t *off_out, int
 
 /* Algorithm 1 as read in R8 (no repair). */
 int32_t orc_greedy_init(const orc_instance *in, int32_t *off_out, int32_t *route_out) {
-  return greedy_core(in, 0, off_out, route_out);
+  return greedy_core(in, 0, NULL, NULL, off_out, route_out);
 }
 
 /* Algorithm 1 with the repair of R12. */
 int32_t orc_greedy_init_repair(const orc_instance *in, int32_t *off_out, int32_t *route_out) {
-  return greedy_core(in, 1, off_out, route_out);
+  return greedy_core(in, 1, NULL, NULL, off_out, route_out);
 }
 
 /* Every canonical move of a schedule: delta = Z(after) - Z(before), flags (feasible,
@@ -648,10 +661,13 @@ int32_t orc_tabu_search(const orc_instance *in, int32_t tenure, int32_t iteratio
 /* ------------------------------------------------------------------------------------
  * Algorithm 2 (Neighbourhood Search) and Algorithm 3 as printed (a per-mission sweep
  * with a tabu list), under these readings:
- *   S1  A sweep takes vehicles i = 0..V-1 in order; the missions j tried for i are i's
- *       route as it stands when i's turn starts, in route order. (During i's turn
- *       missions only leave i, each at most once, so this is well defined.) Trying one
- *       mission is one step; steps are counted from 0 over the whole search.
+ *   S1  A sweep takes the vehicles i in a fixed order, 0..V-1 unless an order is given;
+ *       the missions j tried for i are i's route as it stands when i's turn starts, in
+ *       route order, or by increasing given rank. (During i's turn missions only leave
+ *       i, each at most once, so this is well defined.) The two orders stand for the
+ *       paper's random permutation vectors of the two outer loops, passed in, and stay
+ *       the same for every sweep of the search. Trying one mission is one step; steps
+ *       are counted from 0 over the whole search.
  *   S2  Candidates for j: every other vehicle k (index order) whose type may fly j
  *       (con9), and on k every insertion point q = 0..n_k in order (q = n_k appends).
  *       The first insertion point whose schedule is infeasible (duty cap in HARD mode,
@@ -676,14 +692,28 @@ int32_t orc_tabu_search(const orc_instance *in, int32_t tenure, int32_t iteratio
  *   when nothing was applied, and the objective after the step.
  * ------------------------------------------------------------------------------------ */
 
+/* A permutation of 0..n-1, or NULL. */
+static int is_permutation(const int32_t *p, int n) {
+  if (!p) return 1;
+  char *seen = (char *)calloc((size_t)(n > 0 ? n : 1), 1);
+  int ok = seen != NULL;
+  for (int k = 0; k < n && ok; k++) {
+    if (p[k] < 0 || p[k] >= n || seen[p[k]]) ok = 0;
+    else seen[p[k]] = 1;
+  }
+  free(seen);
+  return ok;
+}
+
 static int sweep_search(const orc_instance *in, int use_tabu, int accept_worse, int32_t tenure,
-                        int32_t max_sweeps, int repair,
+                        int32_t max_sweeps, int repair, const int32_t *vorder, const int32_t *mrank,
                         const int32_t *init_off, const int32_t *init_route, int32_t *best_off,
                         int32_t *best_route, int64_t *z_best_out, int32_t *counts_out,
                         uint32_t *trace_move, int64_t *trace_z, int64_t trace_cap) {
   int rc = check_instance(in);
   if (rc != ORC_OK) return rc;
   int M = in->n_missions, V = in->n_vehicles;
+  if (!is_permutation(vorder, V) || !is_permutation(mrank, M)) return ORC_E_INVALID;
   int32_t *off = (int32_t *)malloc(sizeof(int32_t) * (size_t)(V + 1));
   int32_t *route = (int32_t *)malloc(sizeof(int32_t) * (size_t)(M > 0 ? M : 1));
   int64_t *tabu = (int64_t *)malloc(sizeof(int64_t) * (size_t)(M > 0 ? M : 1) * (size_t)V);
@@ -698,7 +728,7 @@ static int sweep_search(const orc_instance *in, int use_tabu, int accept_worse, 
     if (sched_from_csr(&s, off, route) != ORC_OK || !orc_feasible(in, off, route))
       rc = ORC_E_INFEASIBLE_INIT;
   } else {
-    rc = greedy_core(in, repair, off, route);
+    rc = greedy_core(in, repair, vorder, mrank, off, route);
   }
   sweep_ctx c = {0};
   int64_t sweeps = 0, z_init = 0;
@@ -715,6 +745,8 @@ static int sweep_search(const orc_instance *in, int use_tabu, int accept_worse, 
     c.trace_move = trace_move;
     c.trace_z = trace_z;
     c.trace_cap = trace_cap;
+    c.vorder = vorder;
+    c.mrank = mrank;
     sched_copy(&best_t, &s);
     int go_on = 1;
     while (go_on && sweeps < max_sweeps) {
@@ -743,23 +775,24 @@ static int sweep_search(const orc_instance *in, int use_tabu, int accept_worse, 
 }
 
 /* Algorithm 2 (readings S1-S3, S5), started from Algorithm 1 (with the repair of R12
- * when `repair` is set) unless init_off / init_route give the start.
+ * when `repair` is set) unless init_off / init_route give the start; vorder / mrank
+ * give the loop orders of S1 (NULL: index and route order), each a permutation.
  * z_out[3] = {best, initial, final} objectives;
  * counts_out[4] = {sweeps, moves applied, steps, step of the best (-1: initial)}. */
 int32_t orc_neighbourhood_search(const orc_instance *in, int32_t max_sweeps, int32_t repair,
-                                 const int32_t *init_off,
+                                 const int32_t *vorder, const int32_t *mrank, const int32_t *init_off,
                                  const int32_t *init_route, int32_t *best_off, int32_t *best_route,
                                  int64_t *z_out, int32_t *counts_out, uint32_t *trace_move,
                                  int64_t *trace_z, int64_t trace_cap) {
-  return sweep_search(in, 0, 0, 0, max_sweeps, repair, init_off, init_route, best_off, best_route, z_out,
+  return sweep_search(in, 0, 0, 0, max_sweeps, repair, vorder, mrank, init_off, init_route, best_off, best_route, z_out,
                       counts_out, trace_move, trace_z, trace_cap);
 }
 
 /* Algorithm 3 as printed (readings S1, S2, S4 or S4b, S5); outputs as above. */
 int32_t orc_tabu_sweep(const orc_instance *in, int32_t tenure, int32_t max_sweeps, int32_t accept_worse,
-                       int32_t repair, const int32_t *init_off,
+                       int32_t repair, const int32_t *vorder, const int32_t *mrank, const int32_t *init_off,
                        const int32_t *init_route, int32_t *best_off, int32_t *best_route, int64_t *z_out,
                        int32_t *counts_out, uint32_t *trace_move, int64_t *trace_z, int64_t trace_cap) {
-  return sweep_search(in, 1, accept_worse != 0, tenure, max_sweeps, repair, init_off, init_route, best_off, best_route, z_out,
+  return sweep_search(in, 1, accept_worse != 0, tenure, max_sweeps, repair, vorder, mrank, init_off, init_route, best_off, best_route, z_out,
                       counts_out, trace_move, trace_z, trace_cap);
 }

@@ -307,6 +307,16 @@ def paper_fleet(seed: int, n_missions: int, *, heli_only_frac: float = 0.3) -> I
                          name=f"paper-fleet-s{seed}-m{n_missions}")
 
 
+def sweep_orders(seed: int, n_vehicles: int, n_missions: int):
+    """The random loop orders of one run of the paper's sweeps (its permutation vectors
+    for the loops over bases and over a base's missions): a permutation of the vehicles
+    and a rank for every mission, both uniform, from their own seed."""
+    rng = np.random.default_rng(seed)
+    vorder = rng.permutation(n_vehicles).astype(np.int32)
+    mrank = rng.permutation(n_missions).astype(np.int32)
+    return vorder, mrank
+
+
 def random_instance(seed: int, *, n_loc: int, n_vehicles: int, n_missions: int,
                     n_types: int = 1, max_minutes: int = 300, heli_only_frac: float = 0.0,
                     deadlines: bool = False, deadline_lo: int = 0, horizon: int = 1440,
