@@ -97,6 +97,19 @@ __device__ __forceinline__ int32_t checked(double m, int& bad) {
   return ok ? static_cast<int32_t>(m) : 0;
 }
 
+// Drain a warp's queue of deferred entries: each lane takes entries and writes the
+// float64 result.
+__device__ __forceinline__ void drain(const MParams& P, const double* c, int32_t* base, int L, int64_t LL,
+                                      const int* q, int n, int lane, int& bad) {
+  __syncwarp();
+  for (int k = lane; k < n; k += 32) {
+    const int e = q[k];
+    const int i = e >> 12, j = (e >> 1) & 2047, t = e & 1;
+    base[t * LL + static_cast<int64_t>(i) * L + j] = checked(minutes64(P, c, i, j, t), bad);
+  }
+  __syncwarp();
+}
+
 template <bool HAV>
 __global__ void __launch_bounds__(kWarps * 32) travel_kernel(const __grid_constant__ MParams P) {
   __shared__ Stage st;
