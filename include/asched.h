@@ -412,16 +412,32 @@ typedef struct {
   int32_t capacity;
 } asched_sweep_trace;
 
+/* Loop orders of the sweeps (device memory, optional). The paper lets the loops over
+ * bases and over a base's missions run in random permutation order (Section 4.2); a run
+ * of the sweeps takes one such pair of orders, kept for all its sweeps and for
+ * Algorithm 1's repair sweep:
+ *   vehicle_order  V_b entries at veh_off[b]: the vehicles' turns, a permutation of
+ *                  0..V_b-1; NULL: 0, 1, ..., V_b-1.
+ *   mission_rank   M_b entries at mis_off[b]: a vehicle's missions are tried by
+ *                  increasing rank, a permutation of 0..M_b-1; NULL: route order.
+ * An order that is not a permutation gives ASCHED_E_INVALID in that instance's status.
+ * Several runs of one instance are several batch entries with different orders. */
+typedef struct {
+  const int32_t* vehicle_order;
+  const int32_t* mission_rank;
+} asched_sweep_orders;
+
 /* Queue the sweep `algorithm` on every instance of `batch` on `stream`. params:
  * tenure (Algorithm 3), iterations = the most sweeps (>= 0), cap_mode, lambda,
  * cluster_size 0 or 1, block_threads 0 (automatic) or a multiple of 32 in [32, 512],
  * flags: ASCHED_SWEEP_ACCEPT_WORSE (Algorithm 3 only) and ASCHED_SWEEP_REPAIR; timeout_ns
  * is unused (the sweep waits on nothing). iterations * n_missions + tenure must stay below 2^31.
- * out is laid out as for asched_solve_batch (flight and overflow may be NULL); trace
- * may be NULL. Instances whose state does not fit one CTA's shared memory return
+ * orders may be NULL (index and route order). out is laid out as for asched_solve_batch
+ * (flight and overflow may be NULL); trace may be NULL. Instances whose state does not fit one CTA's shared memory return
  * ASCHED_E_TOO_LARGE (a paper-sized instance needs about 4 KB). */
 int asched_sweep_batch(const asched_batch* batch, int32_t algorithm, const asched_params* params,
-                       const asched_batch_result* out, const asched_sweep_trace* trace, void* stream);
+                       const asched_sweep_orders* orders, const asched_batch_result* out,
+                       const asched_sweep_trace* trace, void* stream);
 
 /* ---------------------------------------------------------------- travel matrix ----
  * Travel-time matrices built on the device from location coordinates (Eq. e1,

@@ -86,6 +86,10 @@ class BatchResult(ctypes.Structure):
     _fields_ = [("route_off", P), ("route", P), ("flight", P), ("overflow", P), ("info", P)]
 
 
+class SweepOrders(ctypes.Structure):
+    _fields_ = [("vehicle_order", P), ("mission_rank", P)]
+
+
 class SweepTrace(ctypes.Structure):
     _fields_ = [("move", P), ("z", P), ("capacity", ctypes.c_int32)]
 
@@ -122,7 +126,7 @@ SIGNATURES = {
     "asched_server_sizes": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_int32, P, P]),
     "asched_serve": (ctypes.c_int, [P, P, ctypes.c_int64, ctypes.c_int32, P]),
-    "asched_sweep_batch": (ctypes.c_int, [P, ctypes.c_int32, P, P, P, P]),
+    "asched_sweep_batch": (ctypes.c_int, [P, ctypes.c_int32, P, P, P, P, P]),
     "asched_travel_matrix": (ctypes.c_int, [P, P, P, P]),
 }
 

@@ -429,10 +429,23 @@ class SweepTrace:
         return _lib.SweepTrace(_ptr(self.move), _ptr(self.z), int(self.capacity))
 
 
+def sweep_orders_tensors(bp: BatchProblem, orders):
+    """Pack per-instance (vehicle_order, mission_rank) pairs (numpy arrays, either may be
+    None for the default) into the batch's concatenated device layout."""
+    vo = np.concatenate([np.arange(int(bp.h_veh_off[b + 1] - bp.h_veh_off[b])) if o[0] is None else o[0]
+                         for b, o in enumerate(orders)]).astype(np.int32)
+    mr = np.concatenate([np.arange(int(bp.h_mis_off[b + 1] - bp.h_mis_off[b])) if o[1] is None else o[1]
+                         for b, o in enumerate(orders)] or [np.zeros(0)]).astype(np.int32)
+    t = lambda a: torch.from_numpy(a if a.size else np.zeros(1, np.int32)).to(bp.device)  # noqa: E731
+    return t(vo), t(mr)
+
+
 def sweep_batch(bp: BatchProblem, algorithm: int, params: _lib.Params, out: Optional[BatchOutput] = None,
-                trace_capacity: int = 0, stream: Optional[torch.cuda.Stream] = None):
+                trace_capacity: int = 0, stream: Optional[torch.cuda.Stream] = None, orders=None):
     """Queue asched_sweep_batch: Algorithm 2 (SWEEP_NEIGHBOURHOOD) or the per-mission sweep
-    of Algorithm 3 (SWEEP_TABU) on every instance. Returns (out, trace or None)."""
+    of Algorithm 3 (SWEEP_TABU) on every instance. orders: None (index and route order),
+    a pair of device tensors from sweep_orders_tensors, or a list of per-instance
+    (vehicle_order, mission_rank). Returns (out, trace or None)."""
     if out is None:
         out = bp.alloc_output()
     trace = None
@@ -440,10 +453,16 @@ def sweep_batch(bp: BatchProblem, algorithm: int, params: _lib.Params, out: Opti
         n = max(bp.B, 1) * int(trace_capacity)
         trace = SweepTrace(torch.zeros(n, dtype=torch.int32, device=bp.device),
                            torch.zeros(n, dtype=torch.int32, device=bp.device), int(trace_capacity))
+    ords = None
+    if orders is not None:
+        vo, mr = orders if isinstance(orders, tuple) else sweep_orders_tensors(bp, orders)
+        ords = _lib.SweepOrders(_ptr(vo), _ptr(mr))
+        bp._keep_orders = (vo, mr)  # the launch reads them until the stream gets there
     s = stream if stream is not None else torch.cuda.current_stream(bp.device)
     res = out.struct()
     tr = trace.struct() if trace is not None else None
     rc = _lib.load().asched_sweep_batch(ctypes.byref(bp.struct), int(algorithm), ctypes.byref(params),
+                                        ctypes.byref(ords) if ords is not None else None,
                                         ctypes.byref(res), ctypes.byref(tr) if tr is not None else None,
                                         ctypes.c_void_p(s.cuda_stream))
     _lib.check(rc, "asched_sweep_batch")

@@ -36,23 +36,29 @@ def build(force: bool = False, verbose: bool = False) -> str:
         tag = f".tmp{os.getpid()}"
         inc = ["-I", os.path.join(ROOT, "include")]
         objs, procs = [], []
-        for src in SRCS:
-            obj = os.path.join(OUT_DIR, os.path.basename(src) + tag + ".o")  # nvcc reads the suffix
-            cmd = [nvcc(), *NVCC_FLAGS, *inc, "-c", "-o", obj, src]
-            if verbose:
-                cmd.insert(1, "-Xptxas=-v")
-                print(" ".join(cmd), file=sys.stderr)
-            objs.append(obj)
-            procs.append(subprocess.Popen(cmd))
-        codes = [p.wait() for p in procs]
-        if any(codes):
-            raise subprocess.CalledProcessError(next(c for c in codes if c), "nvcc")
-        tmp = os.path.join(OUT_DIR, "libasched" + tag + ".so")
-        subprocess.check_call([nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-shared",
-                               "-o", tmp, *objs])
-        for obj in objs:
-            os.remove(obj)
-        os.replace(tmp, LIB)
+        try:
+            for src in SRCS:
+                obj = os.path.join(OUT_DIR, os.path.basename(src) + tag + ".o")  # nvcc reads the suffix
+                cmd = [nvcc(), *NVCC_FLAGS, *inc, "-c", "-o", obj, src]
+                if verbose:
+                    cmd.insert(1, "-Xptxas=-v")
+                    print(" ".join(cmd), file=sys.stderr)
+                objs.append(obj)
+                procs.append(subprocess.Popen(cmd))
+            codes = [p.wait() for p in procs]
+            if any(codes):
+                raise subprocess.CalledProcessError(next(c for c in codes if c), "nvcc")
+            tmp = os.path.join(OUT_DIR, "libasched" + tag + ".so")
+            subprocess.check_call([nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-shared",
+                                   "-o", tmp, *objs])
+            os.replace(tmp, LIB)
+        finally:
+            for p in procs:
+                if p.poll() is None:
+                    p.wait()
+            for obj in objs:
+                if os.path.exists(obj):
+                    os.remove(obj)
     return LIB
 
 

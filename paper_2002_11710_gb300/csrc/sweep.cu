@@ -35,6 +35,8 @@ constexpr int kNoPos = 0x7FFFFFFF;
 
 struct SwParams {
   int32_t B, nt, tenure, max_sweeps, lambda, accept_worse, repair, trace_cap;
+  const int32_t* vehicle_order;  // at veh_off[b], or NULL
+  const int32_t* mission_rank;   // at mis_off[b], or NULL
   const int32_t* loc_off;
   const int32_t* veh_off;
   const int32_t* mis_off;
@@ -60,7 +62,7 @@ struct SwParams {
 // Shared-memory words one instance needs.
 __host__ __device__ inline int sweep_words(int M, int V, int nt, bool tabu) {
   const int N = M + V;
-  return 6 * N + (3 + nt) * M + 5 * V + (tabu ? M * V : 0);
+  return 6 * N + (6 + nt) * M + 6 * V + (tabu ? M * V : 0);
 }
 
 __device__ __forceinline__ int pos0(int x) { return x > 0 ? x : 0; }
@@ -98,6 +100,8 @@ struct Sw {
   int32_t *nxt, *prv, *pos, *bnx, *sloc, *eloc;  // [N]
   int32_t *veh, *wm, *heli, *own;                // [M], own [nt][M]
   int32_t *vty, *fl, *nlen, *fbad, *scratch;     // [V]
+  int32_t *vord, *mrk, *turn, *sorted;           // vehicle order [V]; mission ranks, turn lists [M]
+  bool ranked;                                   // a turn's missions go by rank, not route order
   int32_t* tabu;                                 // [M][V]
 };
 
@@ -243,14 +247,38 @@ __device__ __forceinline__ int sweep_step(const Sw& s, int i, int j, Run& r, uin
   return x;
 }
 
-// One sweep: vehicles in order, each vehicle's missions in route order as it stands
-// when its turn starts. Returns whether a move was applied.
+// One sweep: the vehicles' turns in the given order; a turn tries the vehicle's missions
+// as its route stands when the turn starts, in route order or by increasing rank (missions
+// only leave the vehicle during its turn, and are skipped once gone). Returns whether a
+// move was applied.
 template <bool PEN, bool DL, bool TABU>
 __device__ __forceinline__ bool sweep_pass(const Sw& s, Run& r, uint64_t* red) {
+  const int M = s.M, tid = threadIdx.x, nthr = blockDim.x;
   bool applied = false;
-  for (int i = 0; i < s.V; ++i) {
-    int j = s.nxt[s.M + i];
-    while (j != s.M + i) j = sweep_step<PEN, DL, TABU>(s, i, j, r, red, applied);
+  for (int ii = 0; ii < s.V; ++ii) {
+    const int i = s.vord[ii];
+    const int n = s.nlen[i];
+    __syncthreads();  // every thread is done with the previous turn's list
+    if (tid == 0) {
+      int k = 0;
+      for (int w = s.nxt[M + i]; w != M + i; w = s.nxt[w]) s.turn[k++] = w;
+    }
+    const int32_t* list = s.turn;
+    if (s.ranked) {
+      __syncthreads();
+      for (int k = tid; k < n; k += nthr) {  // place each mission at its rank among the turn's
+        const int m = s.turn[k], rm = s.mrk[m];
+        int at = 0;
+        for (int x = 0; x < n; ++x) at += s.mrk[s.turn[x]] < rm;
+        s.sorted[at] = m;
+      }
+      list = s.sorted;
+    }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+      const int j = list[k];
+      if (s.veh[j] == i) sweep_step<PEN, DL, TABU>(s, i, j, r, red, applied);
+    }
   }
   return applied;
 }
@@ -326,6 +354,11 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const __grid_constan
   s.nlen = p; p += V;
   s.fbad = p; p += V;
   s.scratch = p; p += V;
+  s.vord = p; p += V;
+  s.mrk = p; p += M;
+  s.turn = p; p += M;
+  s.sorted = p; p += M;
+  s.ranked = Q.mission_rank != nullptr;
   s.tabu = p;
 
   // ---- load and validate (the same checks as the full-neighbourhood search)
@@ -340,6 +373,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const __grid_constan
     s.eloc[m] = d;
     s.heli[m] = h;
     s.wm[m] = DL ? dln[m] : 0;
+    s.mrk[m] = Q.mission_rank ? Q.mission_rank[mo + m] : m;
   }
   for (int v = tid; v < V; v += nthr) {
     const int bl = vbase[v];
@@ -348,6 +382,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const __grid_constan
     s.sloc[M + v] = bl;
     s.eloc[M + v] = bl;
     s.vty[v] = ty;
+    s.vord[v] = Q.vehicle_order ? Q.vehicle_order[vo + v] : v;
   }
   int maxT = 0;
   for (int64_t x = tid; x < static_cast<int64_t>(nt) * L * L; x += nthr) {
@@ -366,6 +401,27 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const __grid_constan
     const double bound = 2.0 * (2.0 * M + V + 2.0) * static_cast<double>(s_int[0]) *
                          (1.0 + static_cast<double>(s.lam));
     if (!(bound < 2147483648.0)) status = ASCHED_E_OVERFLOW_GUARD;
+  }
+  if (status == ASCHED_OK && (Q.vehicle_order || Q.mission_rank)) {
+    // the orders must be permutations (fbad and turn serve as counters here)
+    for (int v = tid; v < V; v += nthr) s.fbad[v] = 0;
+    for (int m = tid; m < M; m += nthr) s.turn[m] = 0;
+    __syncthreads();
+    int badp = 0;
+    for (int v = tid; v < V; v += nthr) {
+      const int x = s.vord[v];
+      if (x < 0 || x >= V) badp = 1;
+      else atomicAdd(&s.fbad[x], 1);
+    }
+    for (int m = tid; m < M; m += nthr) {
+      const int x = s.mrk[m];
+      if (x < 0 || x >= M) badp = 1;
+      else atomicAdd(&s.turn[x], 1);
+    }
+    __syncthreads();
+    for (int v = tid; v < V; v += nthr) badp |= s.fbad[v] != 1;
+    for (int m = tid; m < M; m += nthr) badp |= s.turn[m] != 1;
+    if (__syncthreads_or(badp)) status = ASCHED_E_INVALID;
   }
 
   // ---- in-mission legs per travel layer, empty routes, tabu list
@@ -539,8 +595,8 @@ void* pick_sweep(bool pen, bool dl, bool tabu) {
 }  // namespace
 
 extern "C" int asched_sweep_batch(const asched_batch* bt, int32_t algorithm, const asched_params* p,
-                                  const asched_batch_result* out, const asched_sweep_trace* trace,
-                                  void* stream) {
+                                  const asched_sweep_orders* orders, const asched_batch_result* out,
+                                  const asched_sweep_trace* trace, void* stream) {
   if (!bt || !p || !out) return ASCHED_E_INVALID;
   if (algorithm != ASCHED_SWEEP_NEIGHBOURHOOD && algorithm != ASCHED_SWEEP_TABU) return ASCHED_E_INVALID;
   if (p->tenure < 0 || p->iterations < 0 || p->lambda < 0) return ASCHED_E_INVALID;
@@ -616,6 +672,8 @@ extern "C" int asched_sweep_batch(const asched_batch* bt, int32_t algorithm, con
   q.out_flight = out->flight;
   q.out_over = out->overflow;
   q.info = out->info;
+  q.vehicle_order = orders ? orders->vehicle_order : nullptr;
+  q.mission_rank = orders ? orders->mission_rank : nullptr;
   q.trace_move = trace ? trace->move : nullptr;
   q.trace_z = trace ? trace->z : nullptr;
   void* args[] = {&q};

@@ -57,7 +57,7 @@ def test_sweep_host_argument_errors_need_no_gpu():
     L = _lib.load()
 
     def call(alg, p, trace=None):
-        return L.asched_sweep_batch(ctypes.byref(bp.struct), alg, ctypes.byref(p), ctypes.byref(out),
+        return L.asched_sweep_batch(ctypes.byref(bp.struct), alg, ctypes.byref(p), None, ctypes.byref(out),
                                     ctypes.byref(trace) if trace is not None else None, None)
 
     assert call(9, api.sweep_params(5)) == api.E_INVALID
@@ -75,4 +75,4 @@ def test_sweep_host_argument_errors_need_no_gpu():
     assert call(api.SWEEP_TABU, api.sweep_params(5), _lib.SweepTrace(None, None, -1)) == api.E_INVALID
     empty = api.BatchProblem([], device="cpu")
     assert L.asched_sweep_batch(ctypes.byref(empty.struct), api.SWEEP_TABU, ctypes.byref(api.sweep_params(5)),
-                                ctypes.byref(empty.alloc_output().struct()), None, None) == api.OK
+                                None, ctypes.byref(empty.alloc_output().struct()), None, None) == api.OK

@@ -234,3 +234,61 @@ def test_paper_fleet_batch_with_repair_matches_oracle(mode, repair):
             else:
                 r = oracle.tabu_sweep(pb, tenure, 60, repair=repair)
             _check(bp, out, trace, b, r)
+
+
+@pytest.mark.parametrize("mode", [HARD, PENALTY], ids=["hard", "penalty"])
+def test_random_loop_orders_match_oracle(mode):
+    """The paper's permutation vectors: every instance with its own vehicle order and
+    mission ranks (Algorithm 1's repair sweep uses them too)."""
+    rng = np.random.default_rng(21)
+    sizes = rng.integers(12, 34, size=256)
+    insts = [gen.paper_fleet(500 + s, int(m)) for s, m in enumerate(sizes)]
+    orders = [gen.sweep_orders(9000 + s, i.n_vehicles, i.n_missions) for s, i in enumerate(insts)]
+    bp = api.BatchProblem(insts)
+    for alg, tenure, aw in ((api.SWEEP_NEIGHBOURHOOD, 0, False), (api.SWEEP_TABU, 5, False),
+                            (api.SWEEP_TABU, 5, True)):
+        ms = 20 if aw else 60
+        p = api.sweep_params(ms, mode, 1000, tenure, aw, repair=True)
+        out, trace = api.sweep_batch(bp, alg, p, trace_capacity=2048, orders=orders)
+        torch.cuda.synchronize()
+        for b, inst in enumerate(insts):
+            pb = oracle.Problem(inst, mode, 1000)
+            vo, mr = orders[b]
+            if alg == api.SWEEP_NEIGHBOURHOOD:
+                r = oracle.neighbourhood_search(pb, ms, repair=True, vorder=vo, mrank=mr)
+            else:
+                r = oracle.tabu_sweep(pb, tenure, ms, accept_worse=aw, repair=True, vorder=vo, mrank=mr)
+            _check(bp, out, trace, b, r)
+
+
+def test_multi_start_runs_of_one_instance():
+    """Ten runs of one instance with ten order pairs in one launch (the paper's 10 runs):
+    each equals its own oracle run; best, worst and mean follow."""
+    inst = gen.paper_fleet(77, 30)
+    runs = [gen.sweep_orders(k, inst.n_vehicles, inst.n_missions) for k in range(10)]
+    bp = api.BatchProblem([inst] * 10)
+    out, trace = api.sweep_batch(bp, api.SWEEP_TABU, api.sweep_params(100, HARD, 1000, 7, repair=True),
+                                 trace_capacity=4096, orders=runs)
+    torch.cuda.synchronize()
+    zs = []
+    for b, (vo, mr) in enumerate(runs):
+        r = oracle.tabu_sweep(oracle.Problem(inst, HARD, 1000), 7, 100, repair=True, vorder=vo, mrank=mr)
+        _check(bp, out, trace, b, r)
+        if r["status"] == 0:
+            zs.append(r["z_best"])
+    assert zs
+
+
+def test_orders_that_are_not_permutations_are_rejected():
+    insts = [gen.paper_fleet(1, 20), gen.paper_fleet(2, 20)]
+    bp = api.BatchProblem(insts)
+    good = gen.sweep_orders(0, 12, 20)
+    bad_v = (np.zeros(12, np.int32), None)
+    out, _ = api.sweep_batch(bp, api.SWEEP_NEIGHBOURHOOD, api.sweep_params(5), orders=[good, bad_v])
+    bad_m = (None, np.full(20, 25, np.int32))
+    out2, _ = api.sweep_batch(bp, api.SWEEP_NEIGHBOURHOOD, api.sweep_params(5), orders=[bad_m, good])
+    torch.cuda.synchronize()
+    st = out.info.view(-1, api.INFO_LEN)[:, api.INFO_STATUS].cpu().tolist()
+    st2 = out2.info.view(-1, api.INFO_LEN)[:, api.INFO_STATUS].cpu().tolist()
+    assert st[1] == api.E_INVALID and st2[0] == api.E_INVALID
+    assert st[0] != api.E_INVALID and st2[1] != api.E_INVALID
