@@ -348,6 +348,12 @@ def run_batched(args, dev):
             "speedup_vs_sequential": seq_ms / t, "gpu_launches": 2}
 
 
+# Requests of at least BIG_MISSIONS missions go to a launch of BIG_CLUSTERS clusters of
+# BIG_CLUSTER CTAs (chosen by a sweep on this stream: p99 27.1 ms with one-CTA workers
+# only, 5.0 ms with this lane).
+BIG_MISSIONS, BIG_CLUSTER, BIG_CLUSTERS = 60, 8, 8
+
+
 def run_serving(args, dev):
     """The serving workload: Poisson re-planning requests at 2,000 req/s (sizes
     lognormal around 60 missions, clipped to [10, 400], V = ceil(M/5), 1,000 iterations
@@ -363,7 +369,8 @@ def run_serving(args, dev):
     arrivals = gen.poisson_arrivals(7, 2000.0, args.serve_seconds)
     reqs = [pool[k % len(pool)] for k in range(len(arrivals))]
     srv = serve.Server(max_loc=72, max_vehicles=80, max_missions=400, n_slots=4096,
-                       budget_bytes=40 << 30, device=dev)
+                       budget_bytes=40 << 30, device=dev, big_missions=BIG_MISSIONS,
+                       big_cluster=BIG_CLUSTER, big_clusters=BIG_CLUSTERS)
     srv.start(params, idle_timeout_s=60.0)
     try:
         lat, wall = serve.run_stream(srv, reqs, arrivals)
@@ -392,6 +399,9 @@ def run_serving(args, dev):
     wall2 = time.perf_counter() - t0
     return {"workload": (f"Poisson 2,000 req/s for {args.serve_seconds:g} s, M ~ lognormal(median 60) "
                          "in [10, 400], V = ceil(M/5), 1,000 iterations, 40 GB slot budget"),
+            "lanes": {"one_cta": f"requests of fewer than {BIG_MISSIONS} missions, one CTA each",
+                      "clusters": f"requests of {BIG_MISSIONS} missions or more, {BIG_CLUSTERS} clusters "
+                                  f"of {BIG_CLUSTER} CTAs, one cluster per request"},
             "requests": len(reqs), "served": served, "wall_s": wall,
             "solves_per_s": len(reqs) / wall,
             "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3),

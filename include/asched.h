@@ -313,6 +313,7 @@ int asched_solve_batch(const asched_batch* batch, const asched_params* params,
 #define ASCHED_CTRL_STOP 2
 #define ASCHED_CTRL_SERVED 3
 #define ASCHED_CTRL_IDLE_EXITS 4
+#define ASCHED_CTRL_STARTED 5 /* CTAs of the launch that have started */
 #define ASCHED_CTRL_LEN 8
 
 typedef struct {
@@ -335,8 +336,15 @@ int asched_server_sizes(int32_t max_loc, int32_t max_vehicles, int32_t max_missi
                         int32_t* slot_words, int32_t* out_words);
 
 /* Start the serving launch on `stream` (returns at once). max_ctas > 0 caps the number
- * of CTAs (default: every SM). The launch ends once control[ASCHED_CTRL_STOP] is set and
- * every published request has been taken, or after idle_timeout_ns (> 0) without a new
+ * of CTAs (default: every SM). With params->cluster_size C in {2, 4, 8, 16} the launch
+ * is made of clusters of C CTAs (max_ctas / C of them, as many as the device places) and
+ * each request is solved by a whole cluster, as asched_solve with that cluster size:
+ * for the largest requests of a mixed stream, served by a second launch with its own
+ * ring and control words over the same slots. Every CTA adds 1 to
+ * control[ASCHED_CTRL_STARTED] when it starts. The call loads every serving kernel
+ * first, so that a second serving launch started while one runs does not wait for it
+ * (kernels load on first use, and a load can wait for the device to be idle). The launch
+ * ends once control[ASCHED_CTRL_STOP] is set and every published request has been taken, or after idle_timeout_ns (> 0) without a new
  * request (counted in control[ASCHED_CTRL_IDLE_EXITS]). A request whose sizes exceed the
  * capacities, or whose deadline flag differs from has_deadlines, gets ASCHED_E_INVALID
  * in its info[ASCHED_INFO_STATUS]. */

@@ -70,7 +70,7 @@ class Server(ctypes.Structure):
 
 
 SLOT_HEADER = 16
-CTRL_PUBLISHED, CTRL_CLAIMED, CTRL_STOP, CTRL_SERVED, CTRL_IDLE_EXITS = 0, 1, 2, 3, 4
+CTRL_PUBLISHED, CTRL_CLAIMED, CTRL_STOP, CTRL_SERVED, CTRL_IDLE_EXITS, CTRL_STARTED = 0, 1, 2, 3, 4, 5
 CTRL_LEN = 8
 
 

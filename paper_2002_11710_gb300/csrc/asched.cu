@@ -169,6 +169,13 @@ __device__ __forceinline__ void cluster_sync_all() {
                    : "memory");
 }
 
+// The same cluster barrier without .aligned: for code where the threads of a warp may
+// arrive from different paths (the warp is also synchronised first).
+__device__ __forceinline__ void cluster_sync_unaligned() {
+  __syncwarp();
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
 __device__ __forceinline__ uint32_t mapa_rank(uint32_t local_addr, uint32_t rank) {
   uint32_t r;
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_addr), "r"(rank));
@@ -178,6 +185,13 @@ __device__ __forceinline__ uint32_t mapa_rank(uint32_t local_addr, uint32_t rank
 // Store into a peer CTA's shared memory (relaxed, cluster scope).
 __device__ __forceinline__ void st_peer_u64(uint32_t cluster_addr, uint64_t v) {
   asm volatile("st.relaxed.cluster.shared::cluster.u64 [%0], %1;" ::"r"(cluster_addr), "l"(v) : "memory");
+}
+
+// Load a 32-bit word from a peer CTA's shared memory (ordered by a cluster barrier).
+__device__ __forceinline__ int ld_peer_i32(uint32_t cluster_addr) {
+  int v;
+  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(cluster_addr) : "memory");
+  return v;
 }
 
 // Load from this CTA's shared memory, observing peers' relaxed stores.
@@ -1124,7 +1138,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
     P.info[7] = 0;
   }
   // No CTA may leave while a peer can still write into its shared memory.
-  if (C > 1 && looped) cluster_sync_all();
+  if (C > 1 && looped) cluster_sync_unaligned();
 }
 
 template <bool PEN, bool DL, bool DEBUG, bool BIG>
@@ -1255,12 +1269,20 @@ __host__ __device__ inline int serve_out_words(int Vc, int Mc) {
 
 __device__ __forceinline__ int ld_volatile_i32(const int32_t* p) { return *reinterpret_cast<const volatile int32_t*>(p); }
 
-template <bool PEN, bool DL>
+// CL: the launch is made of thread-block clusters of Q.run.cluster CTAs and each request
+// is solved by a whole cluster (the same search as asched_solve with that cluster size):
+// rank 0 claims the ticket and the others read it from rank 0's shared memory between
+// two cluster barriers. Their wait at the barrier ends when rank 0 arrives, which its own
+// bounded claim loop guarantees.
+template <bool PEN, bool DL, bool CL>
 __global__ void __launch_bounds__(kMaxThreads, 1) serve_kernel(const __grid_constant__ SParams Q) {
   __shared__ int s_ticket;
+  const int C = CL ? Q.run.cluster : 1;
+  const int rank = CL ? static_cast<int>(cluster_rank()) : 0;
+  if (threadIdx.x == 0) atomicAdd(&Q.control[ASCHED_CTRL_STARTED], 1);
   uint64_t idle_since = global_ns();
   while (true) {
-    if (threadIdx.x == 0) {
+    if (rank == 0 && threadIdx.x == 0) {
       int got;
       while (true) {
         const int pub = ld_volatile_i32(&Q.control[ASCHED_CTRL_PUBLISHED]);
@@ -1285,9 +1307,16 @@ __global__ void __launch_bounds__(kMaxThreads, 1) serve_kernel(const __grid_cons
       }
       s_ticket = got;
     }
-    __syncthreads();
-    const int t = s_ticket;
-    __syncthreads();
+    int t;
+    if (CL) {
+      cluster_sync_unaligned();  // thread 0 of rank 0 arrives from its claim loop
+      t = rank == 0 ? s_ticket : ld_peer_i32(mapa_rank(smem_u32(&s_ticket), 0));
+      cluster_sync_unaligned();  // every CTA has read it before rank 0 claims the next
+    } else {
+      __syncthreads();
+      t = s_ticket;
+      __syncthreads();
+    }
     if (t < 0) break;
     const int slot = ld_volatile_i32(&Q.ring[t % Q.ring_len]);
     const int32_t* in = Q.slot_data + static_cast<int64_t>(slot) * Q.slot_words;
@@ -1318,20 +1347,20 @@ __global__ void __launch_bounds__(kMaxThreads, 1) serve_kernel(const __grid_cons
     if (sizes_ok) {
       const Layout small = make_layout(M, V, L, Q.nt, false);
       if (!Q.compact && small.total <= Q.smem_words) {
-        solve_one<PEN, DL, false, false>(P, small, 1, 0);
+        solve_one<PEN, DL, false, false>(P, small, C, rank);
       } else {
         const Layout big = make_layout(M, V, L, Q.nt, true);
         if (big.total <= Q.smem_words) {
-          solve_one<PEN, DL, false, true>(P, big, 1, 0);
-        } else if (threadIdx.x == 0) {
+          solve_one<PEN, DL, false, true>(P, big, C, rank);
+        } else if (rank == 0 && threadIdx.x == 0) {
           P.info[ASCHED_INFO_STATUS] = ASCHED_E_TOO_LARGE;
         }
       }
-    } else if (threadIdx.x == 0) {
+    } else if (rank == 0 && threadIdx.x == 0) {
       P.info[ASCHED_INFO_STATUS] = ASCHED_E_INVALID;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (rank == 0 && threadIdx.x == 0) {
       __threadfence_system();
       *reinterpret_cast<volatile int32_t*>(&Q.done[slot]) = gin(in + 6);
       atomicAdd(&Q.control[ASCHED_CTRL_SERVED], 1);
@@ -1592,9 +1621,33 @@ int launch_batch(const asched_batch* bt, const asched_params* p, const asched_ba
   return ASCHED_OK;
 }
 
-template <bool PEN, bool DL>
+template <bool PEN, bool DL, bool CL>
 void* serve_kernel_ptr() {
-  return reinterpret_cast<void*>(&serve_kernel<PEN, DL>);
+  return reinterpret_cast<void*>(&serve_kernel<PEN, DL, CL>);
+}
+
+template <bool CL>
+void* pick_serve(bool pen, bool dl) {
+  return pen ? (dl ? serve_kernel_ptr<true, true, CL>() : serve_kernel_ptr<true, false, CL>())
+             : (dl ? serve_kernel_ptr<false, true, CL>() : serve_kernel_ptr<false, false, CL>());
+}
+
+// Load every serving kernel now. Kernels are loaded on first use, and loading one can
+// wait for the device to go idle: a second persistent launch started while a first one
+// runs (the cluster lane and the one-CTA lane of a server) would then wait until the
+// first ends, which for a persistent launch is only its idle timeout.
+int preload_serve_kernels() {
+  void* fns[] = {pick_serve<false>(false, false), pick_serve<false>(false, true), pick_serve<false>(true, false),
+                 pick_serve<false>(true, true),   pick_serve<true>(false, false),  pick_serve<true>(false, true),
+                 pick_serve<true>(true, false),   pick_serve<true>(true, true)};
+  for (void* fn : fns) {
+    cudaFuncAttributes a;
+    if (cudaFuncGetAttributes(&a, fn) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return ASCHED_E_CUDA;
+    }
+  }
+  return ASCHED_OK;
 }
 
 int launch_serve(const asched_server* sv, const asched_params* p, int64_t idle_ns, int32_t max_ctas, void* stream) {
@@ -1603,13 +1656,16 @@ int launch_serve(const asched_server* sv, const asched_params* p, int64_t idle_n
       sv->max_missions < 0 || sv->n_types < 1 || sv->n_types > 2 || idle_ns <= 0)
     return ASCHED_E_INVALID;
   if (!sv->slot_data || !sv->slot_out || !sv->ring || !sv->control || !sv->done) return ASCHED_E_INVALID;
-  if (p->cluster_size > 1) return ASCHED_E_INVALID;
   asched_instance cap = {};
   cap.n_loc = sv->max_loc;
   cap.n_types = sv->n_types;
   cap.n_vehicles = sv->max_vehicles;
   cap.n_missions = sv->max_missions;
   int rc = check_sizes(&cap, p);
+  if (rc != ASCHED_OK) return rc;
+  const int C = p->cluster_size > 1 ? p->cluster_size : 1;
+  if (C > 1 && max_ctas > 0 && max_ctas < C) return ASCHED_E_INVALID;
+  rc = preload_serve_kernels();
   if (rc != ASCHED_OK) return rc;
   const int limit = max_smem_optin();
   if (limit < 0) return ASCHED_E_CUDA;
@@ -1619,29 +1675,24 @@ int launch_serve(const asched_server* sv, const asched_params* p, int64_t idle_n
   const int64_t bytes = static_cast<int64_t>(lay.total) * 4;
   const bool pen = p->cap_mode == ASCHED_PENALTY;
   const bool dl = sv->has_deadlines != 0;
-  void* fn = pen ? (dl ? serve_kernel_ptr<true, true>() : serve_kernel_ptr<true, false>())
-                 : (dl ? serve_kernel_ptr<false, true>() : serve_kernel_ptr<false, false>());
+  void* fn = C > 1 ? pick_serve<true>(pen, dl) : pick_serve<false>(pen, dl);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)) !=
       cudaSuccess)
     return ASCHED_E_CUDA;
+  if (C > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    return ASCHED_E_CUDA;
   const int threads = p->block_threads ? p->block_threads : kMaxThreads;
-  int dev = 0, sms = 0, per_sm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, static_cast<size_t>(bytes)) !=
-          cudaSuccess) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
     (void)cudaGetLastError();
     return ASCHED_E_CUDA;
   }
-  if (per_sm < 1) return ASCHED_E_TOO_LARGE;
-  int grid = sms * per_sm;
-  if (max_ctas > 0 && max_ctas < grid) grid = max_ctas;
   SParams q = {};
   q.run.nt = sv->n_types;
   q.run.tenure = p->tenure;
   q.run.iterations = p->iterations;
   q.run.lambda = pen ? p->lambda : 0;
-  q.run.cluster = 1;
+  q.run.cluster = C;
   q.run.timeout_ns = p->timeout_ns > 0 ? p->timeout_ns : kDefaultTimeoutNs;
   q.n_slots = sv->n_slots;
   q.ring_len = sv->ring_len;
@@ -1660,8 +1711,41 @@ int launch_serve(const asched_server* sv, const asched_params* p, int64_t idle_n
   q.control = sv->control;
   q.done = sv->done;
   void* args[] = {&q};
-  if (cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, static_cast<size_t>(bytes),
-                       static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = static_cast<size_t>(bytes);
+  cfg.stream = static_cast<cudaStream_t>(stream);
+  cudaLaunchAttribute attr[1];
+  int grid;
+  if (C > 1) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(C, 1, 1);
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, fn, &cfg) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return ASCHED_E_CUDA;
+    }
+    if (clusters < 1) return ASCHED_E_TOO_LARGE;
+    int want = (max_ctas > 0 ? max_ctas : sms) / C;  // whole clusters only
+    grid = C * (want < clusters ? want : clusters);
+  } else {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, static_cast<size_t>(bytes)) !=
+        cudaSuccess) {
+      (void)cudaGetLastError();
+      return ASCHED_E_CUDA;
+    }
+    if (per_sm < 1) return ASCHED_E_TOO_LARGE;
+    grid = sms * per_sm;
+    if (max_ctas > 0 && max_ctas < grid) grid = max_ctas;
+  }
+  cfg.gridDim = dim3(grid, 1, 1);
+  if (cudaLaunchKernelExC(&cfg, fn, args) != cudaSuccess) {
     (void)cudaGetLastError();
     return ASCHED_E_CUDA;
   }

@@ -1,7 +1,10 @@
 """Continuous-batching request server over asched_serve (host side).
 
 The device side is one persistent launch (asched_serve): every CTA takes the next
-published request as soon as it is free. This module owns the host side: a fixed pool
+published request as soon as it is free. Optionally a second persistent launch made of
+thread-block clusters takes the largest requests (at least `big_missions` missions), each
+solved by a whole cluster, so that they do not set the tail latency; it is launched
+first, while the device is idle, and the one-CTA launch takes the remaining SMs. This module owns the host side: a fixed pool
 of device-resident request slots sized by a device-memory budget, admission of new
 requests into free slots while others are running, publication by copies ordered on a
 dedicated stream, and completion polling. All device memory and pinned staging is
@@ -18,7 +21,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import CTRL_LEN, CTRL_PUBLISHED, CTRL_SERVED, CTRL_STOP, SLOT_HEADER
+from ._lib import CTRL_LEN, CTRL_PUBLISHED, CTRL_SERVED, CTRL_STARTED, CTRL_STOP, SLOT_HEADER
 from .api import INFO_LEN, _ptr
 
 
@@ -30,7 +33,8 @@ class Server:
 
     def __init__(self, max_loc: int, max_vehicles: int, max_missions: int, n_types: int = 1,
                  n_slots: int = 1024, has_deadlines: bool = False, budget_bytes: int = 40 << 30,
-                 device="cuda"):
+                 device="cuda", big_missions: Optional[int] = None, big_cluster: int = 16,
+                 big_clusters: int = 1):
         self.device = torch.device(device)
         self.Lc, self.Vc, self.Mc, self.nt = int(max_loc), int(max_vehicles), int(max_missions), int(n_types)
         sw, ow = ctypes.c_int32(0), ctypes.c_int32(0)
@@ -56,6 +60,9 @@ class Server:
         self.stop_stage = torch.ones(1, dtype=torch.int32).pin_memory()
         self.done_host = torch.full((self.n_slots,), -1, dtype=torch.int32).pin_memory()
         self.out_host = torch.zeros(self.out_words, dtype=torch.int32).pin_memory()
+        # control words are read into this pinned buffer: an allocation of pinned memory
+        # while a persistent launch runs could wait for the launch to end
+        self.ctrl_host = torch.zeros(CTRL_LEN, dtype=torch.int32).pin_memory()
         self._stage_np = self.stage.numpy()
         self._ring_np = self.ring_stage.numpy()
         self._pub_np = self.pub_stage.numpy()
@@ -70,13 +77,50 @@ class Server:
         self.struct = _lib.Server(self.n_slots, self.ring_len, self.Lc, self.Vc, self.Mc, self.nt,
                                   int(self.has_deadlines), _ptr(self.slot_data), _ptr(self.slot_out),
                                   _ptr(self.ring), _ptr(self.control), _ptr(self.done))
+        # the large-request lane: its own ring, control words, stream and ticket counter
+        self.big_missions = None if big_missions is None else int(big_missions)
+        self.big_cluster, self.big_clusters = int(big_cluster), int(big_clusters)
+        self.big_ctas = 0
+        if self.big_missions is not None:
+            self.ring_big = torch.zeros(self.ring_len, dtype=torch.int32, device=dev)
+            self.control_big = torch.zeros(CTRL_LEN, dtype=torch.int32, device=dev)
+            self.ring_stage_big = torch.zeros(self.ring_len, dtype=torch.int32).pin_memory()
+            self.pub_stage_big = torch.zeros(self.ring_len, dtype=torch.int32).pin_memory()
+            self._ring_big_np = self.ring_stage_big.numpy()
+            self._pub_big_np = self.pub_stage_big.numpy()
+            self.big_stream = torch.cuda.Stream(device=dev)
+            self.next_ticket_big = 0
+            self.struct_big = _lib.Server(self.n_slots, self.ring_len, self.Lc, self.Vc, self.Mc, self.nt,
+                                          int(self.has_deadlines), _ptr(self.slot_data), _ptr(self.slot_out),
+                                          _ptr(self.ring_big), _ptr(self.control_big), _ptr(self.done))
 
     # ------------------------------------------------------------------ lifecycle
+    def _read_control(self, control, k: int) -> int:
+        with torch.cuda.stream(self.poll_stream):
+            self.ctrl_host[k:k + 1].copy_(control[k:k + 1], non_blocking=True)
+        self.poll_stream.synchronize()
+        return int(self.ctrl_host[k].item())
+
     def start(self, params: _lib.Params, idle_timeout_s: float = 10.0, max_ctas: int = 0):
         torch.cuda.synchronize(self.device)  # buffers are initialised
-        rc = _lib.load().asched_serve(ctypes.byref(self.struct), ctypes.byref(params),
-                                      int(idle_timeout_s * 1e9), int(max_ctas),
-                                      ctypes.c_void_p(self.serve_stream.cuda_stream))
+        L = _lib.load()
+        sms = torch.cuda.get_device_properties(self.device).multi_processor_count
+        if self.big_missions is not None:
+            big = _lib.Params(params.tenure, params.iterations, params.cap_mode, params.lam,
+                              self.big_cluster, params.block_threads, params.timeout_ns, params.flags)
+            want = self.big_cluster * self.big_clusters
+            _lib.check(L.asched_serve(ctypes.byref(self.struct_big), ctypes.byref(big), int(idle_timeout_s * 1e9),
+                                      want, ctypes.c_void_p(self.big_stream.cuda_stream)), "asched_serve (clusters)")
+            # the clusters must be resident before the one-CTA launch fills the device
+            t0 = time.perf_counter()
+            while self._read_control(self.control_big, CTRL_STARTED) < want:
+                if time.perf_counter() - t0 > 5.0:
+                    raise RuntimeError("the cluster launch did not start")
+                time.sleep(1e-3)
+            self.big_ctas = want
+        rest = (max_ctas if max_ctas > 0 else sms) - self.big_ctas
+        rc = L.asched_serve(ctypes.byref(self.struct), ctypes.byref(params), int(idle_timeout_s * 1e9),
+                            int(max(rest, 1)), ctypes.c_void_p(self.serve_stream.cuda_stream))
         _lib.check(rc, "asched_serve")
         self.running = True
 
@@ -86,7 +130,11 @@ class Server:
             return
         with torch.cuda.stream(self.copy_stream):
             self.control[CTRL_STOP:CTRL_STOP + 1].copy_(self.stop_stage, non_blocking=True)
+            if self.big_missions is not None:
+                self.control_big[CTRL_STOP:CTRL_STOP + 1].copy_(self.stop_stage, non_blocking=True)
         self.serve_stream.synchronize()
+        if self.big_missions is not None:
+            self.big_stream.synchronize()
         self.running = False
 
     # ------------------------------------------------------------------ requests
@@ -121,18 +169,27 @@ class Server:
             return None
         slot = self.free.pop()
         used = self.pack(slot, inst, seq)
-        t = self.next_ticket
+        big = self.big_missions is not None and len(inst.pickup) >= self.big_missions
+        if big:
+            t, ring, control = self.next_ticket_big, self.ring_big, self.control_big
+            ring_stage, pub_stage, ring_np, pub_np = (self.ring_stage_big, self.pub_stage_big,
+                                                      self._ring_big_np, self._pub_big_np)
+        else:
+            t, ring, control = self.next_ticket, self.ring, self.control
+            ring_stage, pub_stage, ring_np, pub_np = self.ring_stage, self.pub_stage, self._ring_np, self._pub_np
         r = t % self.ring_len
-        self._ring_np[r] = slot
-        self._pub_np[r] = t + 1
+        ring_np[r] = slot
+        pub_np[r] = t + 1
         self.slot_seq[slot] = seq
         base = slot * self.slot_words
         with torch.cuda.stream(self.copy_stream):
             self.slot_data[base:base + used].copy_(self.stage[slot, :used], non_blocking=True)
-            self.ring[r:r + 1].copy_(self.ring_stage[r:r + 1], non_blocking=True)
-            self.control[CTRL_PUBLISHED:CTRL_PUBLISHED + 1].copy_(self.pub_stage[r:r + 1],
-                                                                  non_blocking=True)
-        self.next_ticket = t + 1
+            ring[r:r + 1].copy_(ring_stage[r:r + 1], non_blocking=True)
+            control[CTRL_PUBLISHED:CTRL_PUBLISHED + 1].copy_(pub_stage[r:r + 1], non_blocking=True)
+        if big:
+            self.next_ticket_big = t + 1
+        else:
+            self.next_ticket = t + 1
         return slot
 
     def poll(self):
@@ -164,16 +221,19 @@ class Server:
                 "info": w[3 * Vc + 1 + Mc:3 * Vc + 1 + Mc + INFO_LEN].copy()}
 
     def served(self) -> int:
-        with torch.cuda.stream(self.poll_stream):
-            v = self.control[CTRL_SERVED:CTRL_SERVED + 1].to("cpu", non_blocking=True)
-        self.poll_stream.synchronize()
-        return int(v.item())
+        n = self._read_control(self.control, CTRL_SERVED)
+        if self.big_missions is not None:
+            n += self._read_control(self.control_big, CTRL_SERVED)
+        return n
 
 
-def run_stream(server: Server, requests, arrivals_s, on_done=None, poll_interval_s: float = 50e-6):
+def run_stream(server: Server, requests, arrivals_s, on_done=None, poll_interval_s: float = 50e-6,
+               stall_timeout_s: float = 30.0):
     """Feed requests at their arrival times (seconds from now) into a started server and
     wait for all of them. Returns per-request latency in seconds (arrival -> completion
-    observed by the host) and the wall time. on_done(i, slot) may read results."""
+    observed by the host) and the wall time. on_done(i, slot) may read results. Raises
+    if requests are pending and none completes for stall_timeout_s (a launch that ended,
+    for instance after its idle timeout, serves nothing more)."""
     n = len(requests)
     lat = np.zeros(n)
     slot_of = {}
@@ -182,6 +242,7 @@ def run_stream(server: Server, requests, arrivals_s, on_done=None, poll_interval
     t0 = time.perf_counter()
     seq_to_req = {}
     completed = 0
+    last_progress = time.perf_counter()
     while completed < n:
         now = time.perf_counter() - t0
         while i < n and arrivals_s[i] <= now:
@@ -199,6 +260,11 @@ def run_stream(server: Server, requests, arrivals_s, on_done=None, poll_interval
                     on_done(seq, slot)
                 pending -= 1
                 completed += 1
+                last_progress = time.perf_counter()
+            if time.perf_counter() - last_progress > stall_timeout_s:
+                raise RuntimeError(f"{pending} requests pending and none completed for {stall_timeout_s:g} s")
+        else:
+            last_progress = time.perf_counter()
         if i < n and not pending:
             wait = arrivals_s[i] - (time.perf_counter() - t0)
             if wait > 2 * poll_interval_s:

@@ -83,3 +83,66 @@ def test_server_launch_ends_by_itself_when_idle():
     assert time.perf_counter() - t0 < 10.0
     torch.cuda.synchronize()
     assert int(srv.control[CTRL_IDLE_EXITS].item()) == 3
+
+
+def test_cluster_lane_results_equal_solving_alone():
+    """Requests of 40 or more missions go to a launch of two 4-CTA clusters, the rest to
+    one-CTA workers; both launches share 6 slots, so admission waits on both. Every
+    result equals solving the request alone."""
+    reqs = [gen.random_instance(800 + k, n_loc=6 + k % 11, n_vehicles=1 + k % 8, n_missions=(13 * k) % 75,
+                                n_types=2, heli_only_frac=0.2 if k % 3 else 0.0, duty_cap=1500,
+                                max_minutes=120) for k in range(40)]
+    assert sum(r.n_missions >= 40 for r in reqs) >= 10
+    params = api.make_params(5, 120, gen.PENALTY, 1000)
+    srv = serve.Server(max_loc=16, max_vehicles=8, max_missions=75, n_types=2, n_slots=6,
+                       big_missions=40, big_cluster=4, big_clusters=2)
+    got = {}
+    srv.start(params, idle_timeout_s=30.0, max_ctas=16)
+    try:
+        assert srv.big_ctas == 8
+        arrivals = np.cumsum(np.random.default_rng(2).exponential(0.0004, size=len(reqs)))
+        serve.run_stream(srv, reqs, arrivals, on_done=lambda i, s: got.__setitem__(i, srv.result(s)))
+    finally:
+        srv.stop()
+    assert sorted(got) == list(range(len(reqs)))
+    assert srv.served() == len(reqs)
+    assert int(srv.control_big[api._lib.CTRL_SERVED].item()) == sum(r.n_missions >= 40 for r in reqs)
+    solved = sum(_compare(got[i], _alone(inst, params), inst.n_vehicles, inst.n_missions)
+                 for i, inst in enumerate(reqs))
+    assert solved >= 0.7 * len(reqs)
+
+
+def test_cluster_lane_ends_by_itself_when_idle():
+    srv = serve.Server(max_loc=8, max_vehicles=4, max_missions=10, n_slots=4, big_missions=5, big_cluster=2,
+                       big_clusters=2)
+    t0 = time.perf_counter()
+    srv.start(api.make_params(3, 10, gen.PENALTY, 1000), idle_timeout_s=0.2, max_ctas=6)
+    srv.serve_stream.synchronize()
+    srv.big_stream.synchronize()
+    assert time.perf_counter() - t0 < 10.0
+    torch.cuda.synchronize()
+    assert int(srv.control[CTRL_IDLE_EXITS].item()) == 2
+    assert int(srv.control_big[CTRL_IDLE_EXITS].item()) == 2  # one per cluster (its rank 0)
+
+
+def test_serving_workload_with_cluster_lane():
+    """The serving workload's stream with requests of 60 or more missions on a launch of
+    8-CTA clusters: every request is served and a sample equals solving it alone."""
+    arrivals = gen.poisson_arrivals(6, 2000.0, 0.1)
+    reqs = [gen.serving_request(11_000 + k) for k in range(len(arrivals))]
+    params = api.params_from(gen.SERVING_PARAMS)
+    srv = serve.Server(max_loc=72, max_vehicles=80, max_missions=400, n_slots=256, big_missions=60,
+                       big_cluster=8, big_clusters=4)
+    got = {}
+    keep = set(range(0, len(reqs), 5))
+    srv.start(params, idle_timeout_s=30.0)
+    try:
+        serve.run_stream(srv, reqs, arrivals,
+                         on_done=lambda i, s: got.__setitem__(i, srv.result(s)) if i in keep else None)
+    finally:
+        srv.stop()
+    assert srv.served() == len(reqs)
+    n_big = sum(r.n_missions >= 60 for r in reqs)
+    assert n_big > 0 and int(srv.control_big[api._lib.CTRL_SERVED].item()) == n_big
+    for i in sorted(keep):
+        assert _compare(got[i], _alone(reqs[i], params), reqs[i].n_vehicles, reqs[i].n_missions)
