@@ -145,44 +145,78 @@ __device__ __forceinline__ int sweep_step(const Sw& s, int i, int j, Run& r, uin
   uint64_t best = kNoKey;
   int my_y = -1, my_ins = 0;
   if (rem_ok) {
-    // pass 1: first infeasible insertion point of every vehicle
-    for (int y = tid; y < N; y += nthr) {
-      const int k = y < M ? s.veh[y] : y - M;
-      if (k == i || k < 0) continue;  // k < 0: a mission Algorithm 1 has not placed yet
+    // Insert j before y (on vehicle k, point q): false if y is not a candidate; else
+    // ins (the change of k's flight), feasibility, and the key when feasible.
+    auto cand = [&](int y, int& k, int& q, int& ins, bool& ok, uint64_t& key) -> bool {
+      k = y < M ? s.veh[y] : y - M;
+      if (k == i || k < 0) return false;  // k < 0: a mission Algorithm 1 has not placed yet
       const int tyk = s.vty[k];
-      if (heli_j && tyk != 0) continue;
-      if (TABU && s.tabu[j * V + k] >= r.step) continue;
+      if (heli_j && tyk != 0) return false;
+      if (TABU && s.tabu[j * V + k] >= r.step) return false;
+      q = s.pos[y];
       const int uy = s.prv[y];
       const int eu = s.eloc[uy], sy = s.sloc[y];
       const int a = tt(s, tyk, eu, pj) + s.own[tyk * M + j];
       const int bq = tt(s, tyk, dj, sy);
-      const int ins = a + bq - (s.nlen[k] == 0 ? 0 : tt(s, tyk, eu, sy));
-      bool ok = true;
+      ins = a + bq - (s.nlen[k] == 0 ? 0 : tt(s, tyk, eu, sy));
+      const int flk = s.fl[k];
+      ok = true;
       if (DL) {
         ok = (uy < M ? s.wm[uy] : 0) + a <= wj;
         ok = ok && (y < M ? wj + bq + s.own[tyk * M + y] <= s.wm[y] : wj + bq <= s.horizon);
       }
-      if (!PEN) ok = ok && s.fl[k] + ins <= cap;
-      if (!ok) atomicMin(&s.fbad[k], s.pos[y]);
+      if (!PEN) ok = ok && flk + ins <= cap;
+      const int d = di + ins + (PEN ? lam * (pos0(flk + ins - cap) - pos0(flk - cap)) : 0);
+      key = cand_key(d, k, q);
+      return true;
+    };
+    // Pass 1: every candidate is evaluated once; an infeasible one marks the first
+    // infeasible insertion point of its vehicle. A thread keeps the keys of its first two
+    // candidates; further ones (more than 2 x threads nodes) are evaluated again in pass 2.
+    uint64_t kk[2];
+    int ky[2], kins[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int y = tid + c * nthr;
+      kk[c] = kNoKey;
+      ky[c] = y;
+      kins[c] = 0;
+      int k, q, ins;
+      bool ok;
+      uint64_t key;
+      if (y < N && cand(y, k, q, ins, ok, key)) {
+        if (ok) {
+          kk[c] = key;
+          kins[c] = ins;
+        } else {
+          atomicMin(&s.fbad[k], q);
+        }
+      }
+    }
+    for (int y = tid + 2 * nthr; y < N; y += nthr) {
+      int k, q, ins;
+      bool ok;
+      uint64_t key;
+      if (cand(y, k, q, ins, ok, key) && !ok) atomicMin(&s.fbad[k], q);
     }
     __syncthreads();
-    // pass 2: least (delta, k, q) before each vehicle's first infeasible point
-    for (int y = tid; y < N; y += nthr) {
-      const int k = y < M ? s.veh[y] : y - M;
-      if (k == i || k < 0) continue;
-      const int tyk = s.vty[k];
-      if (heli_j && tyk != 0) continue;
-      if (TABU && s.tabu[j * V + k] >= r.step) continue;
-      const int q = s.pos[y];
-      if (q >= s.fbad[k]) continue;
-      const int uy = s.prv[y];
-      const int eu = s.eloc[uy], sy = s.sloc[y];
-      const int ins = tt(s, tyk, eu, pj) + s.own[tyk * M + j] + tt(s, tyk, dj, sy) -
-                      (s.nlen[k] == 0 ? 0 : tt(s, tyk, eu, sy));
-      const int flk = s.fl[k];
-      const int d = di + ins + (PEN ? lam * (pos0(flk + ins - cap) - pos0(flk - cap)) : 0);
-      const uint64_t key = cand_key(d, k, q);
-      if (key < best) {
+    // Pass 2: the least (delta, k, q) before each vehicle's first infeasible point.
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const uint64_t key = kk[c];
+      if (key == kNoKey) continue;
+      const int k = static_cast<int>((key >> kIdShift) & 0x3FFu), q = static_cast<int>(key & 0x1FFFu);
+      if (q < s.fbad[k] && key < best) {
+        best = key;
+        my_y = ky[c];
+        my_ins = kins[c];
+      }
+    }
+    for (int y = tid + 2 * nthr; y < N; y += nthr) {
+      int k, q, ins;
+      bool ok;
+      uint64_t key;
+      if (cand(y, k, q, ins, ok, key) && ok && q < s.fbad[k] && key < best) {
         best = key;
         my_y = y;
         my_ins = ins;
@@ -313,8 +347,11 @@ __device__ __forceinline__ uint64_t greedy_pick(const Sw& s, int m, uint64_t* re
   return block_min(key, red);
 }
 
-template <bool PEN, bool DL, bool TABU>
-__global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const __grid_constant__ SwParams Q) {
+// ONE_WARP: the 32-thread launch of small instances, bounded to 64 registers so that 32
+// CTAs (the most an SM holds) are resident; otherwise up to 512 threads.
+template <bool PEN, bool DL, bool TABU, bool ONE_WARP>
+__global__ void __launch_bounds__(ONE_WARP ? 32 : kMaxThreads, ONE_WARP ? 32 : 1)
+    sweep_kernel(const __grid_constant__ SwParams Q) {
   extern __shared__ __align__(16) int32_t g_sw[];
   __shared__ uint64_t s_red[kMaxThreads / 32];
   __shared__ int s_int[4];
@@ -578,18 +615,23 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const __grid_constan
   }
 }
 
-template <bool PEN, bool DL, bool TABU>
+template <bool PEN, bool DL, bool TABU, bool W>
 void* sweep_ptr() {
-  return reinterpret_cast<void*>(&sweep_kernel<PEN, DL, TABU>);
+  return reinterpret_cast<void*>(&sweep_kernel<PEN, DL, TABU, W>);
 }
 
-void* pick_sweep(bool pen, bool dl, bool tabu) {
+template <bool W>
+void* pick_sweep_w(bool pen, bool dl, bool tabu) {
   if (pen) {
-    if (dl) return tabu ? sweep_ptr<true, true, true>() : sweep_ptr<true, true, false>();
-    return tabu ? sweep_ptr<true, false, true>() : sweep_ptr<true, false, false>();
+    if (dl) return tabu ? sweep_ptr<true, true, true, W>() : sweep_ptr<true, true, false, W>();
+    return tabu ? sweep_ptr<true, false, true, W>() : sweep_ptr<true, false, false, W>();
   }
-  if (dl) return tabu ? sweep_ptr<false, true, true>() : sweep_ptr<false, true, false>();
-  return tabu ? sweep_ptr<false, false, true>() : sweep_ptr<false, false, false>();
+  if (dl) return tabu ? sweep_ptr<false, true, true, W>() : sweep_ptr<false, true, false, W>();
+  return tabu ? sweep_ptr<false, false, true, W>() : sweep_ptr<false, false, false, W>();
+}
+
+void* pick_sweep(bool pen, bool dl, bool tabu, bool one_warp) {
+  return one_warp ? pick_sweep_w<true>(pen, dl, tabu) : pick_sweep_w<false>(pen, dl, tabu);
 }
 
 }  // namespace
@@ -639,7 +681,7 @@ extern "C" int asched_sweep_batch(const asched_batch* bt, int32_t algorithm, con
   int threads = p->block_threads;
   if (threads == 0) threads = max_nodes <= 64 ? 32 : max_nodes <= 256 ? 64 : max_nodes <= 1024 ? 128 : 256;
   const size_t bytes = static_cast<size_t>(max_words) * 4;
-  void* fn = pick_sweep(p->cap_mode == ASCHED_PENALTY, bt->deadline != nullptr, tabu);
+  void* fn = pick_sweep(p->cap_mode == ASCHED_PENALTY, bt->deadline != nullptr, tabu, threads == 32);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)) !=
       cudaSuccess) {
     (void)cudaGetLastError();
