@@ -43,8 +43,8 @@ OPS_SWAP = 34
 # DRAM bytes (read + write) of one solve launch, from the ncu capture summarised in
 # profiles/tabu_kernel_paper_shaped.md. Valid only for the kernel source it was taken
 # on; any other source reports traffic as null.
-TRAFFIC_BYTES = 108032
-TRAFFIC_SOURCE_SHA = "cc16eaa723e351ba"
+TRAFFIC_BYTES = 109824
+TRAFFIC_SOURCE_SHA = "4a9dc633abe24688"
 
 
 def _env_int(k, d):

@@ -146,3 +146,37 @@ def test_serving_workload_with_cluster_lane():
     assert n_big > 0 and int(srv.control_big[api._lib.CTRL_SERVED].item()) == n_big
     for i in sorted(keep):
         assert _compare(got[i], _alone(reqs[i], params), reqs[i].n_vehicles, reqs[i].n_missions)
+
+
+_FRESH = r"""
+import sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from paper_2002_11710_gb300 import api, gen, serve
+reqs = [gen.serving_request(12_000 + k) for k in range(40)]
+params = api.params_from(gen.SERVING_PARAMS)
+srv = serve.Server(max_loc=72, max_vehicles=80, max_missions=400, n_slots=64, big_missions=60,
+                   big_cluster=8, big_clusters=2)
+srv.start(params, idle_timeout_s=20.0)   # the cluster launch is this process's first kernel
+try:
+    lat, wall = serve.run_stream(srv, reqs, np.zeros(len(reqs)), stall_timeout_s=15.0)
+finally:
+    srv.stop()
+assert srv.served() == len(reqs)
+print("served", srv.served(), "in %.2f s" % wall)
+"""
+
+
+def test_cluster_lane_first_in_a_fresh_process():
+    """Regression: in a fresh process the one-CTA launch's kernel is not loaded yet when
+    the cluster launch is already running; starting it must not wait for the cluster
+    launch to end (the server preloads its kernels)."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _FRESH.format(root=root)], capture_output=True, text=True,
+                       timeout=180)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "served 40" in r.stdout
