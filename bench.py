@@ -311,8 +311,9 @@ def run_batched(args, dev):
     p = gen.BATCHED_PARAMS
     moves = sum(api.num_moves(i.n_missions, i.n_vehicles) for i in insts) * p.iterations
     bp = api.BatchProblem(insts, dev)
-    thr, tune = api.autotune_batch(bp, api.params_from(p))
-    params = api.params_from(p, block_threads=thr)
+    choice, tune = api.autotune_batch(bp, api.params_from(p))
+    params = api.tuned_params(api.params_from(p), choice)
+    thr = {"block_threads": choice[0], "layout": "int16 matrix" if choice[1] else "gather tables"}
     graph, out = api.capture_batch(bp, params)
     for _ in range(max(1, args.warmup // 2)):
         graph.replay()
@@ -343,7 +344,8 @@ def run_batched(args, dev):
     return {"workload": "1,024 instances, V ~ U[3,30], M ~ U[10,200], 2,000 iterations each, "
                         "replayed from a captured CUDA graph",
             "ms": t, "solves_per_s": 1024 / t * 1e3, "moves_per_s": moves / t * 1e3,
-            "block_threads": thr, "autotune_ms": tune, "instances_ok": ok,
+            "launch_shape": thr, "autotune_ms": {f"{t}{'/int16' if c else ''}": v for (t, c), v in tune.items()},
+            "instances_ok": ok,
             "sequential_ms": seq_ms, "sequential_solves_per_s": 1024 / seq_ms * 1e3,
             "speedup_vs_sequential": seq_ms / t, "gpu_launches": 2}
 

@@ -351,17 +351,22 @@ def solve_batch(bp: BatchProblem, params: _lib.Params, out: Optional[BatchOutput
     return out
 
 
-def autotune_batch(bp: BatchProblem, params: _lib.Params, candidates=(512, 384, 256, 128),
+def autotune_batch(bp: BatchProblem, params: _lib.Params,
+                   candidates=((512, False), (384, False), (256, False), (256, True), (128, True)),
                    probe_iterations: int = 200, repeats: int = 2):
-    """Pick the block size for a batch by timing short probe runs of each candidate
-    (CUDA events on the current stream). Results never depend on the choice; only the
-    time does. Returns (best block size, {candidate: ms})."""
-    probe = _lib.Params(params.tenure, min(params.iterations, probe_iterations), params.cap_mode,
-                        params.lam, params.cluster_size, 0, params.timeout_ns, params.flags)
+    """Pick the launch shape of a batch by timing short probe runs of each candidate
+    (CUDA events on the current stream): (block threads, compact) pairs, compact meaning
+    the int16 matrix layout for every instance (smaller state, more resident CTAs) instead
+    of the gather tables where they fit; a plain int is a block size with the tables.
+    Results never depend on the choice; only the time does. Returns (best candidate,
+    {candidate: ms}) with candidates as (threads, compact) pairs."""
     out = bp.alloc_output()
     times = {}
-    for thr in candidates:
-        probe.block_threads = int(thr)
+    for cand in candidates:
+        thr, compact = (cand, False) if isinstance(cand, int) else (int(cand[0]), bool(cand[1]))
+        probe = _lib.Params(params.tenure, min(params.iterations, probe_iterations), params.cap_mode,
+                            params.lam, params.cluster_size, thr, params.timeout_ns,
+                            (params.flags & ~COMPACT_LAYOUT) | (COMPACT_LAYOUT if compact else 0))
         solve_batch(bp, probe, out=out)  # warm-up
         best = None
         for _ in range(repeats):
@@ -373,8 +378,16 @@ def autotune_batch(bp: BatchProblem, params: _lib.Params, candidates=(512, 384, 
             b.synchronize()
             ms = a.elapsed_time(b)
             best = ms if best is None else min(best, ms)
-        times[int(thr)] = best
+        times[(thr, compact)] = best
     return min(times, key=times.get), times
+
+
+def tuned_params(params: _lib.Params, choice) -> _lib.Params:
+    """params with the launch shape an autotune_batch choice names."""
+    thr, compact = choice
+    return _lib.Params(params.tenure, params.iterations, params.cap_mode, params.lam, params.cluster_size,
+                       int(thr), params.timeout_ns,
+                       (params.flags & ~COMPACT_LAYOUT) | (COMPACT_LAYOUT if compact else 0))
 
 
 def solve_batch_static(bp: BatchProblem, params: _lib.Params, out: Optional[BatchOutput] = None,

@@ -137,9 +137,14 @@ def test_batch_independent_of_block_size_and_autotuner_picks_a_candidate():
     for o in outs[1:]:
         for b in range(len(insts)):
             _same(bp.unpack(outs[0], b), bp.unpack(o, b))
-    best, times = api.autotune_batch(bp, api.make_params(4, 30, PENALTY, 1000), candidates=(256, 128),
-                                     probe_iterations=10, repeats=1)
-    assert best in (256, 128) and set(times) == {256, 128}
+    best, times = api.autotune_batch(bp, api.make_params(4, 30, PENALTY, 1000),
+                                     candidates=((256, False), (128, True)), probe_iterations=10, repeats=1)
+    assert best in ((256, False), (128, True)) and set(times) == {(256, False), (128, True)}
+    tuned = api.tuned_params(api.make_params(4, 30, PENALTY, 1000), best)
+    got = api.solve_batch(bp, tuned)
+    torch.cuda.synchronize()
+    for b in range(len(insts)):
+        _same(bp.unpack(outs[0], b), bp.unpack(got, b))
 
 
 def test_batch_replayed_from_a_cuda_graph_matches_direct_calls():
