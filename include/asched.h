@@ -202,6 +202,26 @@ int asched_solve(const asched_instance* inst, const asched_params* params,
                  const int32_t* init_route_off, const int32_t* init_route,
                  const asched_result* out, void* stream);
 
+/* The same calls under the names of the problem statement's interface: host-side
+ * validation, the device workspace a single-instance search needs (none: every piece of
+ * its state lives in shared memory, so *bytes is set to 0), Algorithm 1 alone, and the
+ * Tabu search.
+ *   asched_validate        = asched_check_instance_host (HOST arrays, no CUDA call).
+ *   asched_workspace_bytes sizes are checked as by asched_plan; *bytes = 0.
+ *   asched_greedy_init     Algorithm 1 (Section 4.1) on the device: the greedy schedule
+ *                          written as device CSR route_off [V + 1] / route [M] and its
+ *                          objective etc. in info [ASCHED_INFO_LEN] (a search of 0
+ *                          iterations); device status ASCHED_E_INFEASIBLE_INIT when a
+ *                          mission fits no vehicle.
+ *   asched_tabu_solve      = asched_solve. */
+int asched_validate(const asched_instance* inst, const asched_params* params);
+int asched_workspace_bytes(const asched_instance* inst, const asched_params* params, size_t* bytes);
+int asched_greedy_init(const asched_instance* inst, const asched_params* params, int32_t* route_off,
+                       int32_t* route, int32_t* info, void* stream);
+int asched_tabu_solve(const asched_instance* inst, const asched_params* params,
+                      const int32_t* init_route_off, const int32_t* init_route,
+                      const asched_result* out, void* stream);
+
 /* Every canonical move of one schedule, for checking (one launch, no move applied).
  *   route_off/route  device CSR schedule (must be feasible).
  *   tabu_until       device [n_missions][n_vehicles] int32, or NULL for none tabu.

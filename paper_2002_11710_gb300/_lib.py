@@ -128,6 +128,10 @@ SIGNATURES = {
     "asched_serve": (ctypes.c_int, [P, P, ctypes.c_int64, ctypes.c_int32, P]),
     "asched_sweep_batch": (ctypes.c_int, [P, ctypes.c_int32, P, P, P, P, P]),
     "asched_travel_matrix": (ctypes.c_int, [P, P, P, P]),
+    "asched_validate": (ctypes.c_int, [P, P]),
+    "asched_workspace_bytes": (ctypes.c_int, [P, P, P]),
+    "asched_greedy_init": (ctypes.c_int, [P, P, P, P, P, P]),
+    "asched_tabu_solve": (ctypes.c_int, [P, P, P, P, P, P]),
 }
 
 _lock = threading.Lock()

@@ -195,6 +195,18 @@ def solve(dp: DeviceProblem, params: _lib.Params, init=None, out: Optional[Solve
     return out
 
 
+def greedy_init(dp: DeviceProblem, params: _lib.Params, stream: Optional[torch.cuda.Stream] = None):
+    """Algorithm 1 alone on the device (asched_greedy_init): (route_off, route, info)
+    device tensors; read them after synchronising the stream."""
+    z = lambda n: torch.zeros(max(n, 1), dtype=torch.int32, device=dp.device)  # noqa: E731
+    off, route, info = z(dp.V + 1), z(dp.M), z(INFO_LEN)
+    s = stream if stream is not None else torch.cuda.current_stream(dp.device)
+    rc = _lib.load().asched_greedy_init(ctypes.byref(dp.struct), ctypes.byref(params), _ptr(off), _ptr(route),
+                                        _ptr(info), ctypes.c_void_p(s.cuda_stream))
+    _lib.check(rc, "asched_greedy_init")
+    return off, route, info
+
+
 def eval_neighbourhood(dp: DeviceProblem, params: _lib.Params, route_off: torch.Tensor,
                        route: torch.Tensor, tabu_until: Optional[torch.Tensor], it: int,
                        z_best: int, with_ids: bool = True,

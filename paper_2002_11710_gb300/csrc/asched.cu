@@ -70,7 +70,7 @@ constexpr int kBufWordsPerNode = 15;
 // and random columns both spread over the banks; tabu stamps are int16 there too.
 struct Layout {  // offsets in int32 words from the start of dynamic shared memory
   int A, B, tabu, cmat, wm, eloc, sloc, vtype, tyl, tym, st0, st1, best, order, cnt, gend, gdep, gfl,
-      glast, misc, warpkey, slots, total;
+      glast, misc, mbar, warpkey, slots, total;
   int Mp, Np, Vp, buf, Ls;
   bool big;
 };
@@ -113,6 +113,7 @@ __host__ __device__ inline Layout make_layout(int M, int V, int L, int nt, bool 
   y.gfl = o;     o += y.Vp;
   y.glast = o;   o += y.Vp;
   y.misc = o;    o += 16;
+  y.mbar = o;    o += 2;  // one mbarrier (8 bytes; o is even here)
   o = round_up(o, 4);
   y.warpkey = o; o += 2 * 32;
   y.slots = o;   o += 2 * 2 * kMaxCluster;
@@ -199,6 +200,48 @@ __device__ __forceinline__ uint64_t ld_own_u64(uint32_t cta_addr) {
   uint64_t v;
   asm volatile("ld.relaxed.cluster.shared::cta.u64 %0, [%1];" : "=l"(v) : "r"(cta_addr) : "memory");
   return v;
+}
+
+// ---- bulk copies global -> shared completing on an mbarrier (compact layout staging)
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// before the barrier's memory serves anything else (the next instance of a persistent
+// launch may lay shared memory out differently)
+__device__ __forceinline__ void mbar_inval(uint32_t bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bytes from global src into this CTA's shared dst (both 16-byte aligned, bytes a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+// the same into the shared memory (same offsets) of every CTA of the cluster in mask
+__device__ __forceinline__ void bulk_g2s_multicast(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar,
+                                                   uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], %4;" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(bar), "h"(mask)
+      : "memory");
+}
+// OR of a flag into a word of another CTA's shared memory
+__device__ __forceinline__ void red_or_peer(uint32_t cluster_addr, uint32_t v) {
+  asm volatile("red.shared::cluster.or.b32 [%0], %1;" ::"r"(cluster_addr), "r"(v) : "memory");
 }
 
 // Instance inputs are read through L2 only (ld.global.cg): a persistent launch reuses
@@ -301,7 +344,7 @@ __device__ inline Smem carve(const Layout& y) {
 }
 
 // misc slots
-enum { MISC_BAD = 0, MISC_MAXT, MISC_Z0, MISC_GREEDY_FAIL, MISC_CSR_BAD };
+enum { MISC_BAD = 0, MISC_MAXT, MISC_Z0, MISC_GREEDY_FAIL, MISC_CSR_BAD, MISC_STAGE_FAIL };
 
 struct Ctx {  // per-launch constants every thread keeps in registers
   int M, V, N, L, Mp, cap, horizon, lam;
@@ -558,6 +601,108 @@ __device__ __forceinline__ uint64_t eval_swap(const Smem& sm, const Tab<BIG>& tb
 
 // ------------------------------------------------------------------ the kernel -----
 
+// The compact layout's int16 matrix, row t*L + r of layer t at T16 + (t*L + r) * Ls, zero
+// padded, built from the int32 input through a staging buffer: the second record buffer,
+// which nothing uses before the first move is applied. When the input is 16-byte aligned
+// its words go by bulk copies completing on an mbarrier, in chunks the size of the
+// buffer; with C > 1 CTAs, rank 0 issues each chunk once, multicast into every CTA of the
+// cluster, so the cluster reads the matrix from L2 once instead of C times. A cluster
+// barrier before each chunk keeps the buffer free until every CTA has converted the
+// previous one. Every wait is bounded by P.timeout_ns; a CTA that gives up tells rank 0,
+// and every CTA reads that at the next barrier, so all leave the loop together. Entries
+// are checked (>= 0) and their maximum taken on the way. Returns true on a timeout.
+__device__ __forceinline__ bool stage_matrix16(const KParams& P, const Layout& lay, int C, int rank, int& bad,
+                                               int& maxT) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int L = P.L, nt = P.nt, Ls = lay.Ls, pad = lay.Ls - P.L;
+  int16_t* T16 = reinterpret_cast<int16_t*>(g_smem + lay.A);
+  for (int i = tid; i < nt * L * pad; i += nthr) {
+    const int r = i / pad;
+    T16[r * Ls + L + (i - r * pad)] = 0;
+  }
+  auto put = [&](int g, int x) {
+    bad |= x < 0;
+    maxT = x > maxT ? x : maxT;
+    const int r = g / L;
+    T16[r * Ls + (g - r * L)] = static_cast<int16_t>(x);
+  };
+  const int words = nt * L * L;
+  const bool aligned = (reinterpret_cast<uintptr_t>(P.travel) & 15u) == 0;
+  const int bulk = aligned ? (words & ~3) : 0;  // words that go by bulk copies (16-byte units)
+  for (int g = bulk + tid; g < words; g += nthr) put(g, gin(P.travel + g));
+  if (bulk == 0) return false;
+  int32_t* stage = g_smem + lay.st1;
+  const int cap = lay.buf & ~3;
+  const uint32_t bar = smem_u32(g_smem + lay.mbar);
+  const uint32_t fail_addr = smem_u32(&g_smem[lay.misc + MISC_STAGE_FAIL]);
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+  }
+  bool gave_up = false;  // this CTA's wait ran out
+  bool stop = false;     // some CTA's did (the same in every CTA)
+  uint32_t phase = 0;
+  for (int c0 = 0; c0 < bulk && !stop; c0 += cap, phase ^= 1u) {
+    const int n = bulk - c0 < cap ? bulk - c0 : cap;
+    if (tid == 0) mbar_arrive_expect_tx(bar, static_cast<uint32_t>(n) * 4u);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // reads of the last chunk before the copy
+    if (C > 1) {
+      cluster_sync_unaligned();
+      stop = ld_peer_i32(mapa_rank(fail_addr, 0)) != 0;
+    } else {
+      __syncthreads();
+      stop = g_smem[lay.misc + MISC_STAGE_FAIL] != 0;
+    }
+    if (stop) break;
+    if (tid == 0 && rank == 0) {
+      if (C > 1)
+        bulk_g2s_multicast(smem_u32(stage), P.travel + c0, static_cast<uint32_t>(n) * 4u, bar,
+                           static_cast<uint16_t>((1u << C) - 1u));
+      else
+        bulk_g2s(smem_u32(stage), P.travel + c0, static_cast<uint32_t>(n) * 4u, bar);
+    }
+    bool ok = mbar_try_wait(bar, phase);
+    if (!ok) {
+      const uint64_t t0 = global_ns();
+      while (!(ok = mbar_try_wait(bar, phase))) {
+        if (static_cast<int64_t>(global_ns() - t0) > P.timeout_ns) break;
+      }
+    }
+    if (!__all_sync(0xffffffffu, ok)) ok = false;
+    if (!ok) {
+      gave_up = true;
+      if ((tid & 31) == 0) {
+        if (C > 1)
+          red_or_peer(mapa_rank(fail_addr, 0), 1u);
+        else
+          atomicOr(&g_smem[lay.misc + MISC_STAGE_FAIL], 1);
+      }
+      continue;  // the next barrier ends the loop in every CTA
+    }
+    for (int i = tid; i < n; i += nthr) put(c0 + i, stage[i]);
+  }
+  if (!stop) {  // every chunk converted: one more barrier, so a failure reported at the end is seen
+    if (C > 1) {
+      cluster_sync_unaligned();
+      stop = ld_peer_i32(mapa_rank(fail_addr, 0)) != 0;
+    } else {
+      __syncthreads();
+      stop = g_smem[lay.misc + MISC_STAGE_FAIL] != 0;
+    }
+  }
+  if (gave_up) {  // let a copy still in flight land (bounded) before this CTA moves on
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, phase ^ 1u) && static_cast<int64_t>(global_ns() - t0) < P.timeout_ns) {
+    }
+  }
+  if (C > 1)
+    cluster_sync_unaligned();  // nobody reads rank 0's flag after this
+  else
+    __syncthreads();  // nobody waits on the barrier after this
+  if (tid == 0) mbar_inval(bar);
+  return stop;
+}
+
 // One complete search (prologue, every iteration, epilogue) of the instance in P by
 // the C CTAs of this cluster (this CTA is `rank`), with shared memory laid out by lay.
 template <bool PEN, bool DL, bool DEBUG, bool BIG>
@@ -606,14 +751,25 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
     sm.tym[v] = ty * Mp;
   }
   int maxT = 0;
-  for (int i = tid; i < nt * L * L; i += nthr) {
-    const int x = gin(P.travel + i);
-    bad |= x < 0;
-    maxT = x > maxT ? x : maxT;
+  if (!BIG) {  // the compact layout checks the matrix while it stages it (prologue 2)
+    for (int i = tid; i < nt * L * L; i += nthr) {
+      const int x = gin(P.travel + i);
+      bad |= x < 0;
+      maxT = x > maxT ? x : maxT;
+    }
+  }
+  if (__syncthreads_or(bad)) status = ASCHED_E_INVALID;
+  if (BIG && status == ASCHED_OK) {
+    // ---- prologue 1b: the int16 matrix, staged through shared memory by bulk copies
+    // (one multicast copy per chunk for the whole cluster), checked as it is converted
+    int tbad = 0;
+    const bool timed_out = stage_matrix16(P, lay, C, rank, tbad, maxT);
+    if (__syncthreads_or(tbad)) status = ASCHED_E_INVALID;
+    if (timed_out) status = ASCHED_E_TIMEOUT;  // the same in every CTA of the cluster
   }
   maxT = __reduce_max_sync(0xffffffffu, maxT);
   if (lane == 0) atomicMax(&sm.misc[MISC_MAXT], maxT);
-  if (__syncthreads_or(bad)) status = ASCHED_E_INVALID;
+  __syncthreads();
   if (BIG && status == ASCHED_OK && sm.misc[MISC_MAXT] > 32767) status = ASCHED_E_TOO_LARGE;
   if (status == ASCHED_OK) {
     // 2 (2M + V + 2) maxT (1 + lambda) < 2^31 keeps every int32 sum in range.
@@ -625,14 +781,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
   // ---- prologue 2: gather tables, in-mission legs, tabu stamps, route ends
   const State S0 = sm.st(0);
   if (status == ASCHED_OK) {
-    if (BIG) {
-      int16_t* T16 = reinterpret_cast<int16_t*>(g_smem + lay.A);
-      const int Ls = lay.Ls;
-      for (int i = tid; i < nt * L * Ls; i += nthr) {
-        const int r = i / Ls, j = i - r * Ls;
-        T16[i] = static_cast<int16_t>(j < L ? gin(P.travel + static_cast<int64_t>(r) * L + j) : 0);
-      }
-    } else {
+    if (!BIG) {
       for (int i = tid; i < nt * L * Mp; i += nthr) {
         const int r = i / Mp, m = i - r * Mp;
         const int t = r / L, l = r - t * L;
@@ -1858,6 +2007,35 @@ int asched_solve(const asched_instance* inst, const asched_params* params, const
   kp.traj_move = out->traj_move;
   kp.traj_z = out->traj_z;
   return launch(inst, params, false, kp, stream);
+}
+
+int asched_validate(const asched_instance* inst, const asched_params* params) {
+  return asched_check_instance_host(inst, params);
+}
+
+int asched_workspace_bytes(const asched_instance* inst, const asched_params* params, size_t* bytes) {
+  if (!bytes) return ASCHED_E_INVALID;
+  const int rc = check_sizes(inst, params);
+  if (rc != ASCHED_OK) return rc;
+  *bytes = 0;
+  return ASCHED_OK;
+}
+
+int asched_greedy_init(const asched_instance* inst, const asched_params* params, int32_t* route_off,
+                       int32_t* route, int32_t* info, void* stream) {
+  if (!params || !route_off || !route || !info) return ASCHED_E_INVALID;
+  asched_params p0 = *params;
+  p0.iterations = 0;
+  asched_result out = {};
+  out.route_off = route_off;
+  out.route = route;
+  out.info = info;
+  return asched_solve(inst, &p0, nullptr, nullptr, &out, stream);
+}
+
+int asched_tabu_solve(const asched_instance* inst, const asched_params* params, const int32_t* init_route_off,
+                      const int32_t* init_route, const asched_result* out, void* stream) {
+  return asched_solve(inst, params, init_route_off, init_route, out, stream);
 }
 
 int asched_batch_workspace_bytes(int32_t n_instances, size_t* out) {

@@ -99,3 +99,22 @@ def test_plan_without_a_device_reports_cuda_error():
     out = _lib.Plan()
     rc = _lib.load().asched_plan(ctypes.byref(s), ctypes.byref(_params()), ctypes.byref(out))
     assert rc == api.E_CUDA
+
+
+def test_validate_and_workspace_entry_points_need_no_gpu():
+    """asched_validate is the host validation under the interface's name;
+    asched_workspace_bytes reports that a single search needs no device workspace."""
+    L = _lib.load()
+    base = gen.random_instance(5, n_loc=6, n_vehicles=3, n_missions=8)
+    bad = gen.Instance(**{**base.__dict__, "pickup": np.where(np.arange(8) == 2, 6, base.pickup)})
+    for inst in (base, gen.paper_shaped(0), bad):
+        s, keep = api.host_struct(inst)
+        p = _params()
+        assert L.asched_validate(ctypes.byref(s), ctypes.byref(p)) == api.check_instance_host(inst, p)
+    s, keep = api.host_struct(gen.paper_shaped(0))
+    n = ctypes.c_size_t(123)
+    assert L.asched_workspace_bytes(ctypes.byref(s), ctypes.byref(_params()), ctypes.byref(n)) == api.OK
+    assert n.value == 0
+    assert L.asched_workspace_bytes(ctypes.byref(s), ctypes.byref(_params(cap_mode=9)),
+                                    ctypes.byref(n)) == api.E_INVALID
+    assert L.asched_workspace_bytes(ctypes.byref(s), ctypes.byref(_params()), None) == api.E_INVALID

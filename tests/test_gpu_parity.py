@@ -161,7 +161,7 @@ def test_trajectory_independent_of_launch_shape(cluster, threads):
     _check_solve_vs_oracle(inst, PENALTY, 6, 80, cluster_size=cluster, block_threads=threads)
 
 
-@pytest.mark.parametrize("mk,mode", [
+GREEDY_CASES = [
     (lambda: gen.tiny(0), PENALTY),
     (lambda: gen.paper_model(7, 24), HARD),
     (lambda: gen.random_instance(61, n_loc=10, n_vehicles=5, n_missions=30, n_types=2,
@@ -171,7 +171,10 @@ def test_trajectory_independent_of_launch_shape(cluster, threads):
                                  heli_only_frac=0.25, deadlines=True, deadline_lo=800,
                                  duty_cap=2500, max_minutes=60), HARD),
     (lambda: gen.large(0), PENALTY),
-])
+]
+
+
+@pytest.mark.parametrize("mk,mode", GREEDY_CASES)
 def test_greedy_init_matches_oracle(mk, mode):
     inst = mk()
     pb = oracle.Problem(inst, mode, 1000)
@@ -192,6 +195,43 @@ def test_greedy_init_matches_oracle(mk, mode):
     np.testing.assert_array_equal(out.route_off.cpu().numpy()[: pb.V + 1], off)
     np.testing.assert_array_equal(out.route.cpu().numpy()[: pb.M], route)
     assert info[api.INFO_Z_BEST] == oracle.cost(pb, off, route)[0]
+
+
+@pytest.mark.parametrize("mk,mode", GREEDY_CASES)
+def test_greedy_init_entry_point_matches_oracle(mk, mode):
+    """asched_greedy_init: Algorithm 1 alone, as its own entry point."""
+    inst = mk()
+    pb = oracle.Problem(inst, mode, 1000)
+    rc, off, route = oracle.greedy_init(pb)
+    dp = api.DeviceProblem(inst)
+    g_off, g_route, info = api.greedy_init(dp, api.make_params(5, 50, mode, 1000))
+    torch.cuda.synchronize()
+    info = info.cpu().numpy()
+    if rc != 0:
+        assert info[api.INFO_STATUS] == api.E_INFEASIBLE_INIT
+        return
+    assert info[api.INFO_STATUS] == 0 and info[api.INFO_ITERS] == 0
+    np.testing.assert_array_equal(g_off.cpu().numpy()[: pb.V + 1], off)
+    np.testing.assert_array_equal(g_route.cpu().numpy()[: pb.M], route)
+    assert info[api.INFO_Z_BEST] == info[api.INFO_Z_INIT] == oracle.cost(pb, off, route)[0]
+
+
+def test_tabu_solve_entry_point_equals_solve():
+    import ctypes
+
+    inst = gen.random_instance(72, n_loc=9, n_vehicles=4, n_missions=17, duty_cap=2000, n_types=2,
+                               heli_only_frac=0.2)
+    dp = api.DeviceProblem(inst)
+    params = api.make_params(5, 80, PENALTY, 1000)
+    a = api.solve(dp, params, trajectory=True)
+    b = api.alloc_output(dp, params.iterations, trajectory=True)
+    res = b.struct()
+    rc = api._lib.load().asched_tabu_solve(ctypes.byref(dp.struct), ctypes.byref(params), None, None,
+                                           ctypes.byref(res), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == api.OK
+    torch.cuda.synchronize()
+    for k in ("route_off", "route", "info", "traj_move", "traj_z"):
+        assert torch.equal(getattr(a, k), getattr(b, k)), k
 
 
 def test_solve_from_given_schedule():
