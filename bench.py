@@ -524,7 +524,54 @@ def run_sweeps(args, dev):
             out[name]["cpu_oracle"] = {"solves_per_s": 256 / dt, "cores": 1,
                                        "sample": f"first 256 distinct instances, {dt:.2f} s"}
     out["multi_start"] = run_multi_start(args, distinct, res, dev)
+    out["single_instance"] = run_sweep_latency(dev)
     return out
+
+
+# The paper's per-instance runtimes (seconds; Python + Numba on an i9-7920X, its CUDA
+# variants on a GTX 1080 Ti), its Table 1, by number of missions: context, not a target.
+PAPER_RUNTIME_S = {
+    12: {"ns": 0.0153, "ns_cuda": 0.548, "tabu": 0.0245, "tabu_cuda": 0.578},
+    15: {"ns": 0.0244, "ns_cuda": 0.532, "tabu": 0.0349, "tabu_cuda": 0.615},
+    18: {"ns": 0.0322, "ns_cuda": 0.544, "tabu": 0.0424, "tabu_cuda": 0.575},
+    21: {"ns": 0.0446, "ns_cuda": 0.519, "tabu": 0.0553, "tabu_cuda": 0.507},
+    24: {"ns": 0.0499, "ns_cuda": 0.611, "tabu": 0.0618, "tabu_cuda": 0.642},
+    27: {"ns": 0.0565, "ns_cuda": 0.618, "tabu": 0.0675, "tabu_cuda": 0.561},
+    30: {"ns": 0.0581, "ns_cuda": 0.599, "tabu": 0.0682, "tabu_cuda": 0.645},
+    33: {"ns": 0.0631, "ns_cuda": 0.686, "tabu": 0.0689, "tabu_cuda": 0.611},
+}
+
+
+def run_sweep_latency(dev):
+    """One paper-fleet instance per launch at the paper's sizes (12-33 missions, its fleet),
+    Algorithm 2 and Algorithm 3 (tenure 7), repair on, HARD cap: device time per solve
+    (CUDA events around the launch, median of 20), beside the paper's own runtimes."""
+    import torch
+
+    from paper_2002_11710_gb300 import api, gen
+
+    res = {}
+    for m in sorted(PAPER_RUNTIME_S):
+        inst = gen.paper_fleet(90_000 + m, m)
+        bp = api.BatchProblem([inst], dev)
+        row = {"paper_s": PAPER_RUNTIME_S[m]}
+        for name, alg in (("algorithm_2_ms", api.SWEEP_NEIGHBOURHOOD), ("algorithm_3_ms", api.SWEEP_TABU)):
+            params = api.sweep_params(100, api.HARD, 1000, 7, repair=True)
+            out, _ = api.sweep_batch(bp, alg, params)
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(20):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                api.sweep_batch(bp, alg, params, out=out)
+                b.record()
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            row[name] = statistics.median(ts)
+            row["status"] = int(out.info[api.INFO_STATUS].item())
+        res[str(m)] = row
+    return res
 
 
 def run_multi_start(args, distinct, default_res, dev):
