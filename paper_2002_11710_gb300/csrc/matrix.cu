@@ -117,6 +117,8 @@ __global__ void __launch_bounds__(kWarps * 32) travel_kernel(const __grid_consta
   __shared__ unsigned s_mag;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float two_r32 = static_cast<float>(P.two_r);
+  const float k0 = P.k32[0], k1 = P.k32[1];
+  const int nt = P.nt;
   int bad = 0;
   for (int b = blockIdx.x; b < P.B; b += gridDim.x) {
     const int lo = P.loc_off[b];
@@ -155,6 +157,7 @@ __global__ void __launch_bounds__(kWarps * 32) travel_kernel(const __grid_consta
     int n = 0;  // queued entries (warp-uniform)
     for (int i = warp; i < L; i += kWarps) {
       int32_t* row = base + static_cast<int64_t>(i) * L;
+      int32_t* row1 = row + LL;  // the same row of the second type's matrix
       for (int j0 = 0; j0 < L; j0 += 32) {
         const int j = j0 + lane;
         const bool live = j < L;
@@ -180,12 +183,13 @@ __global__ void __launch_bounds__(kWarps * 32) travel_kernel(const __grid_consta
           abs_part = 1e-6f;
           magk = 9.536743e-7f * S;  // 2^-20 S
         }
-        for (int t = 0; t < P.nt; ++t) {
-          const float t32 = __fmul_rn(d32, P.k32[t]);
-          const float tol = rel * t32 + P.k32[t] * magk + abs_part;
+        // One entry of type t: rounded in float32 when sure, else queued for float64.
+        auto emit = [&](int t, float kt, int32_t* rowt) {
+          const float t32 = __fmul_rn(d32, kt);
+          const float tol = rel * t32 + kt * magk + abs_part;
           const float frac = t32 - floorf(t32);  // exact for 0 <= t32 < 2^22
           const bool sure = screen && t32 >= 0.0f && t32 < 4194304.0f && fabsf(frac - 0.5f) > tol;
-          if (live && sure) row[t * LL + j] = static_cast<int32_t>(rintf(t32));
+          if (live && sure) rowt[j] = static_cast<int32_t>(rintf(t32));
           const unsigned need = __ballot_sync(0xffffffffu, live && !sure);
           if (need) {
             if (n + 32 > kQueue) {
@@ -195,6 +199,27 @@ __global__ void __launch_bounds__(kWarps * 32) travel_kernel(const __grid_consta
             if (live && !sure) q[n + __popc(need & ((1u << lane) - 1u))] = (i << 12) | (j << 1) | t;
             n += __popc(need);
           }
+        };
+        if (HAV) {  // (this loop, written out, measured faster here than through emit)
+          for (int t = 0; t < P.nt; ++t) {
+            const float t32 = __fmul_rn(d32, P.k32[t]);
+            const float tol = rel * t32 + P.k32[t] * magk + abs_part;
+            const float frac = t32 - floorf(t32);  // exact for 0 <= t32 < 2^22
+            const bool sure = screen && t32 >= 0.0f && t32 < 4194304.0f && fabsf(frac - 0.5f) > tol;
+            if (live && sure) row[t * LL + j] = static_cast<int32_t>(rintf(t32));
+            const unsigned need = __ballot_sync(0xffffffffu, live && !sure);
+            if (need) {
+              if (n + 32 > kQueue) {
+                drain(P, c, base, L, LL, q, n, lane, bad);
+                n = 0;
+              }
+              if (live && !sure) q[n + __popc(need & ((1u << lane) - 1u))] = (i << 12) | (j << 1) | t;
+              n += __popc(need);
+            }
+          }
+        } else {  // constant indices keep both types' constants in registers
+          emit(0, k0, row);
+          if (nt > 1) emit(1, k1, row1);
         }
       }
     }
