@@ -18,10 +18,11 @@
 // Bounds on the float32 time t (every float32 value of a coordinate is off by at most
 // 2^-24 of its magnitude):
 //   Euclidean  coordinates staged as float32; the differences add at most 2^-24 of the
-//              sum of the four magnitudes, then differences, squares, sum, correctly
-//              rounded square root and the product with a rounded 60 / speed add below
-//              6 * 2^-24 relative; screened at 2e-6 t + (60 / speed) 2^-20 S + 1e-6, S the
-//              instance's largest |x| + |y|;
+//              sum of the four magnitudes, then differences, squares, sum, square root
+//              and the product with a rounded 60 / speed add below 6 * 2^-24 relative with
+//              a correctly rounded root, 10 * 2^-24 with the root as a * rsqrtf(a) (rsqrtf
+//              within 2 ulp, CUDA's documented bound, plus one rounded product); screened
+//              at 2e-6 t + (60 / speed) 2^-20 S + 1e-6, S the instance's largest |x| + |y|;
 //   Haversine  angles staged as float pairs hi + lo (lo = float(v - hi)), so a difference
 //              (hi_i - hi_j) + (lo_i - lo_j) is within 2 * 2^-24 of itself plus 2^-47 of
 //              the magnitudes; half-angle differences, sinf (2 ulp), squares, cos(phi)
@@ -29,16 +30,32 @@
 //              number below 1.9 for sqrt(a) <= 0.9 (larger values go to float64 outright)
 //              add below 1.8e-6 relative; screened at 8e-6 t + (60 / speed) 2 r 2^-40
 //              (sum of |angles|) + 1e-5.
-// Times of 2^22 minutes or more also go to float64. The float64 path is the expression
-// above, on the original float64 coordinates. Lanes that need it queue (row, column,
-// type) in shared memory, and the whole warp drains its queue when it fills and at the
-// end of the instance, so float64 work runs on full warps and follows the number of such
-// entries.
+// Times of 2^22 minutes or more also go to float64. The float32 time is rounded by adding
+// and subtracting 1.5 * 2^23: for 0 <= t < 2^22 the sum lies in [2^23, 2^24), where the
+// float32 spacing is 1, so the addition itself rounds t half to even, the integer is the
+// sum's low mantissa bits, and t minus the rounded value is exact (Sterbenz), which gives
+// the distance to the nearest half minute without a conversion instruction. The float64
+// path is the expression above, on the original float64 coordinates. Lanes that need it
+// queue (row, column, type) in shared memory, so float64 work runs on full warps and
+// follows the number of such entries: large instances keep a queue per warp, drained when
+// it fills and at the end of the instance; small instances one queue per CTA, drained
+// after the pairs by as many warps as it has entries (one, as a rule), entries beyond its
+// capacity computed where they arise.
 //
-// One CTA per instance (grid-stride over instances): the instance's coordinates are
-// staged once in shared memory (angles in radians and cos(phi) for Haversine); warps
-// take rows, lanes take columns, so a row's writes are contiguous. An instance with more
-// locations than the stage holds goes through float64 alone.
+// One CTA per instance (grid-stride over instances); the instance's coordinates are
+// staged once in shared memory (angles in radians and cos(phi) for Haversine).
+//   Small instances (n_types * L^2 + 3 <= kOut words, L <= kSmallLoc: L <= 63 for two
+//   types) are built whole in shared memory. Both distances are symmetric in every rounded
+//   operation (x_i - x_j = -(x_j - x_i) exactly, products commute), so each unordered pair
+//   i <= j is evaluated once and written to (i, j) and (j, i). The L (L + 1) / 2 pairs are
+//   numbered row by row with row i folded onto row L - 1 - i (L + 1 pairs per folded row),
+//   so the threads take consecutive numbers with no idle lanes at row ends. The finished
+//   matrices, contiguous in the output, leave by one bulk copy (cp.async.bulk, shared to
+//   global) on their 16-byte aligned middle and plain stores on the at most 3 + 3 words
+//   around it; the next instance waits only for the copy's reads of shared memory.
+//   Larger instances: warps take rows, lanes take columns, so a row's writes are
+//   contiguous. An instance with more locations than the stage holds goes through float64
+//   alone.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -48,8 +65,12 @@
 namespace {
 
 constexpr int kStageLocations = 2048;  // 5 floats per location: 40 KB of shared memory
+constexpr int kSmallLoc = 96;          // locations of an instance built in shared memory
+constexpr int kOut = 8192;             // int32 words of that instance's matrices
 constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
 constexpr int kQueue = 128;  // deferred float64 entries per warp
+constexpr int kCtaQueue = kWarps * kQueue;  // the same words as one queue per CTA (small instances)
 
 struct MParams {
   int32_t B, nt, metric;
@@ -68,26 +89,47 @@ struct Stage {  // structure of arrays: hi and lo of both coordinates, cos(phi)
   float cphi[kStageLocations];
 };
 
+struct SmallStage {
+  float4 hl[kSmallLoc];       // (x hi, y hi, x lo, y lo)
+  float cphi[kSmallLoc];      // float(cos(phi))
+  double cos64[kSmallLoc];    // cos(phi) in float64, as the definition computes it
+  int32_t out[kOut];          // the instance's matrices, offset so that they share the output's 16-byte phase
+};
+
+union SharedStage {
+  Stage big;
+  SmallStage small;
+};
+
 __device__ __forceinline__ double euclid(double xi, double yi, double xj, double yj) {
   const double dx = __dsub_rn(xi, xj), dy = __dsub_rn(yi, yj);
   return __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
 }
 
-__device__ __forceinline__ double haversine(double lati, double loni, double latj, double lonj, double two_r,
-                                            double deg) {
+// Eq. e1 with the cosines of both latitudes given (each equals cos(lat * deg) bit for bit).
+__device__ __forceinline__ double haversine(double lati, double loni, double latj, double lonj, double ci, double cj,
+                                            double two_r, double deg) {
   const double phi_i = __dmul_rn(lati, deg), phi_j = __dmul_rn(latj, deg);
   const double s1 = sin(__dmul_rn(__dsub_rn(phi_i, phi_j), 0.5));
   const double s2 = sin(__dmul_rn(__dsub_rn(__dmul_rn(loni, deg), __dmul_rn(lonj, deg)), 0.5));
-  const double a = __dadd_rn(__dmul_rn(s1, s1), __dmul_rn(__dmul_rn(cos(phi_i), cos(phi_j)), __dmul_rn(s2, s2)));
+  const double a = __dadd_rn(__dmul_rn(s1, s1), __dmul_rn(__dmul_rn(ci, cj), __dmul_rn(s2, s2)));
   const double r = __dsqrt_rn(a);
   return __dmul_rn(two_r, asin(r > 1.0 ? 1.0 : r));  // a NaN stays NaN, as in the definition
 }
 
-// The definition in float64: distance, then rint(d / speed * 60).
-__device__ __forceinline__ double minutes64(const MParams& P, const double* c, int i, int j, int t) {
+// The definition in float64: distance, then rint(d / speed * 60). cos64: the staged
+// cosines of the latitudes (Haversine, small instances) or NULL.
+__device__ __forceinline__ double minutes64(const MParams& P, const double* c, const double* cos64, int i, int j,
+                                            int t) {
   const double xi = c[2 * i], yi = c[2 * i + 1], xj = c[2 * j], yj = c[2 * j + 1];
-  const double d = P.metric == ASCHED_METRIC_HAVERSINE ? haversine(xi, yi, xj, yj, P.two_r, P.deg)
-                                                       : euclid(xi, yi, xj, yj);
+  double d;
+  if (P.metric == ASCHED_METRIC_HAVERSINE) {
+    const double ci = cos64 ? cos64[i] : cos(__dmul_rn(xi, P.deg));
+    const double cj = cos64 ? cos64[j] : cos(__dmul_rn(xj, P.deg));
+    d = haversine(xi, yi, xj, yj, ci, cj, P.two_r, P.deg);
+  } else {
+    d = euclid(xi, yi, xj, yj);
+  }
   return rint(__dmul_rn(__ddiv_rn(d, P.speed[t]), 60.0));
 }
 
@@ -97,29 +139,188 @@ __device__ __forceinline__ int32_t checked(double m, int& bad) {
   return ok ? static_cast<int32_t>(m) : 0;
 }
 
-// Drain a warp's queue of deferred entries: each lane takes entries and writes the
-// float64 result.
+// One float32 time t32 >= 0 (or NaN): its integer in v, and whether that integer is
+// certain, i.e. t32 < 2^22 lies farther than tol = rel t32 + c from every half minute.
+__device__ __forceinline__ bool round_screened(float t32, float rel, float c, int32_t& v) {
+  const float s = __fadd_rn(t32, 12582912.0f);  // 1.5 * 2^23: rounds t32 half to even
+  const float gap = __fsub_rn(0.5f, fabsf(__fsub_rn(t32, __fsub_rn(s, 12582912.0f))));
+  v = __float_as_int(s) - 0x4B400000;
+  return t32 < 4194304.0f && gap > __fmaf_rn(rel, t32, c);
+}
+
+// Drain a warp's queue of deferred entries into the output rows: each lane takes entries
+// and writes the float64 result.
 __device__ __forceinline__ void drain(const MParams& P, const double* c, int32_t* base, int L, int64_t LL,
                                       const int* q, int n, int lane, int& bad) {
   __syncwarp();
   for (int k = lane; k < n; k += 32) {
     const int e = q[k];
     const int i = e >> 12, j = (e >> 1) & 2047, t = e & 1;
-    base[t * LL + static_cast<int64_t>(i) * L + j] = checked(minutes64(P, c, i, j, t), bad);
+    base[t * LL + static_cast<int64_t>(i) * L + j] = checked(minutes64(P, c, nullptr, i, j, t), bad);
   }
   __syncwarp();
 }
 
+// One deferred entry of a small instance: the pair (i, j), i <= j, of type t goes to both
+// of its places in the shared-memory matrix.
+__device__ __forceinline__ void resolve_small(const MParams& P, const double* c, const double* cos64, int32_t* o,
+                                              int L, int e, int& bad) {
+  const int i = e >> 12, j = (e >> 1) & 2047, t = e & 1;
+  const int32_t v = checked(minutes64(P, c, cos64, i, j, t), bad);
+  o[t * L * L + i * L + j] = v;
+  o[t * L * L + j * L + i] = v;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Queue the lanes whose entry of type t is not certain in the CTA's queue (warp-uniform
+// call); an entry past the queue's capacity is computed here.
+__device__ __forceinline__ void enqueue(bool mine, int i, int j, int t, int* cq, unsigned& s_qn, int lane,
+                                        const MParams& P, const double* c, const double* cos64, int32_t* o, int L,
+                                        int& bad) {
+  const unsigned m = __ballot_sync(0xffffffffu, mine);
+  if (!m) return;
+  const int leader = __ffs(m) - 1;
+  unsigned base = 0;
+  if (lane == leader) base = atomicAdd(&s_qn, static_cast<unsigned>(__popc(m)));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (!mine) return;
+  const unsigned pos = base + __popc(m & ((1u << lane) - 1u));
+  const int e = (i << 12) | (j << 1) | t;
+  if (pos < kCtaQueue)
+    cq[pos] = e;
+  else
+    resolve_small(P, c, cos64, o, L, e, bad);
+}
+
+// A small instance, built whole in shared memory and written out by one bulk copy.
 template <bool HAV>
-__global__ void __launch_bounds__(kWarps * 32) travel_kernel(const __grid_constant__ MParams P) {
-  __shared__ Stage st;
+__device__ __forceinline__ void small_instance(const MParams& P, SmallStage& st, int* cq, unsigned& s_qn,
+                                               unsigned& s_mag, const double* c, int32_t* dst, int L, int& bad) {
+  const int lane = threadIdx.x & 31;
+  const int nt = P.nt;
+  for (int l = threadIdx.x; l < L; l += kThreads) {
+    double x = c[2 * l], y = c[2 * l + 1];
+    if (HAV) {
+      x *= P.deg;
+      y *= P.deg;
+    }
+    const float xh = static_cast<float>(x), yh = static_cast<float>(y);
+    if (HAV) {
+      const double cx = cos(x);
+      st.cos64[l] = cx;
+      st.cphi[l] = static_cast<float>(cx);
+      st.hl[l] = make_float4(xh, yh, static_cast<float>(x - static_cast<double>(xh)),
+                             static_cast<float>(y - static_cast<double>(yh)));
+    } else {
+      st.hl[l] = make_float4(xh, yh, 0.0f, 0.0f);
+      atomicMax(&s_mag, __float_as_uint(fabsf(xh) + fabsf(yh)));  // NaN's bits exceed every finite value
+    }
+  }
+  __syncthreads();
+  const int phase = static_cast<int>((reinterpret_cast<uintptr_t>(dst) >> 2) & 3u);
+  int32_t* o = st.out + phase;  // o[w] is dst[w]; both 16-byte aligned at the same w
+  const int LL = L * L;
+  const float k0 = P.k32[0], k1 = P.k32[1];
+  float c0, c1;  // the absolute part of each type's tolerance
+  const float rel = HAV ? 8e-6f : 2e-6f;
+  const float two_r32 = static_cast<float>(P.two_r);
+  if (!HAV) {
+    const float magk = 9.536743e-7f * __uint_as_float(s_mag);  // 2^-20 S
+    c0 = k0 * magk + 1e-6f;
+    c1 = k1 * magk + 1e-6f;
+  }
+  // Pair p = f (L + 1) + k: row f from column f (k < L - f), else row L - 1 - f from column k - 1.
+  const int L1 = L + 1, E = L * L1 / 2;
+  int f = threadIdx.x / L1, k = threadIdx.x - f * L1;
+  const int df = kThreads / L1, dk = kThreads - df * L1;
+  for (int p0 = 0; p0 < E; p0 += kThreads) {
+    const bool live = p0 + static_cast<int>(threadIdx.x) < E;
+    int i = f, j = f + k;
+    if (k >= L - f) {
+      i = L - 1 - f;
+      j = k - 1;
+    }
+    if (!live) i = j = 0;
+    f += df;
+    k += dk;
+    if (k >= L1) {
+      k -= L1;
+      ++f;
+    }
+    const float4 a = st.hl[i], b = st.hl[j];
+    float d32;
+    bool screen = true;
+    if (HAV) {
+      const float dx = __fadd_rn(__fsub_rn(a.x, b.x), __fsub_rn(a.z, b.z));
+      const float dy = __fadd_rn(__fsub_rn(a.y, b.y), __fsub_rn(a.w, b.w));
+      const float s1 = sinf(__fmul_rn(dx, 0.5f)), s2 = sinf(__fmul_rn(dy, 0.5f));
+      const float h = __fadd_rn(__fmul_rn(s1, s1), __fmul_rn(__fmul_rn(st.cphi[i], st.cphi[j]), __fmul_rn(s2, s2)));
+      const float r = __fsqrt_rn(h);
+      screen = r <= 0.9f;
+      d32 = __fmul_rn(two_r32, asinf(r));
+      const float magk = two_r32 * 9.094947e-13f *  // 2 r 2^-40 (sum of |angles|)
+                         (fabsf(a.x) + fabsf(b.x) + fabsf(a.y) + fabsf(b.y));
+      c0 = k0 * magk + 1e-5f;
+      c1 = k1 * magk + 1e-5f;
+    } else {
+      const float dx = __fsub_rn(a.x, b.x), dy = __fsub_rn(a.y, b.y);
+      const float q = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+      d32 = q > 0.0f ? __fmul_rn(q, rsqrtf(q)) : q;  // sqrt(0) = 0 exactly; NaN stays NaN
+    }
+    int32_t v0, v1 = 0;
+    const bool sure0 = round_screened(__fmul_rn(d32, k0), rel, c0, v0) && screen;
+    const bool sure1 = nt < 2 || (round_screened(__fmul_rn(d32, k1), rel, c1, v1) && screen);
+    if (live && sure0) {
+      o[i * L + j] = v0;
+      o[j * L + i] = v0;
+    }
+    if (live && sure1 && nt > 1) {
+      o[LL + i * L + j] = v1;
+      o[LL + j * L + i] = v1;
+    }
+    if (__ballot_sync(0xffffffffu, live && !(sure0 && sure1))) {  // rare: float64 for these
+      enqueue(live && !sure0, i, j, 0, cq, s_qn, lane, P, c, st.cos64, o, L, bad);
+      if (nt > 1) enqueue(live && !sure1, i, j, 1, cq, s_qn, lane, P, c, st.cos64, o, L, bad);
+    }
+  }
+  __syncthreads();  // the queue is complete
+  const int nq = min(static_cast<int>(s_qn), kCtaQueue);
+  for (int e = threadIdx.x; e < nq; e += kThreads) resolve_small(P, c, st.cos64, o, L, cq[e], bad);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the writes above, before the bulk copy reads them
+  __syncthreads();
+  const int W = nt * LL;
+  const int head = min((4 - phase) & 3, W);
+  const int mid = (W - head) & ~3;
+  if (threadIdx.x == 0) {
+    if (mid > 0) {
+      asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst + head),
+                   "r"(smem_addr(o + head)), "r"(static_cast<uint32_t>(mid) * 4u)
+                   : "memory");
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+    s_mag = 0u;  // every thread has read it and the queue's length
+    s_qn = 0u;
+  }
+  if (threadIdx.x < head) dst[threadIdx.x] = o[threadIdx.x];
+  const int w = head + mid + static_cast<int>(threadIdx.x);
+  if (w < W) dst[w] = o[w];
+}
+
+template <bool HAV>
+__global__ void __launch_bounds__(kThreads, 4) travel_kernel(const __grid_constant__ MParams P) {
+  __shared__ __align__(16) SharedStage sh;
   __shared__ int queue[kWarps][kQueue];
-  __shared__ unsigned s_mag;
+  __shared__ unsigned s_mag, s_qn;
+  Stage& st = sh.big;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float two_r32 = static_cast<float>(P.two_r);
   const float k0 = P.k32[0], k1 = P.k32[1];
   const int nt = P.nt;
   int bad = 0;
+  if (threadIdx.x == 0) s_mag = s_qn = 0u;
   for (int b = blockIdx.x; b < P.B; b += gridDim.x) {
     const int lo = P.loc_off[b];
     const int L = P.loc_off[b + 1] - lo;
@@ -129,12 +330,17 @@ __global__ void __launch_bounds__(kWarps * 32) travel_kernel(const __grid_consta
     if (L > kStageLocations) {  // float64 only
       for (int i = warp; i < L; i += kWarps)
         for (int j = lane; j < L; j += 32)
-          for (int t = 0; t < P.nt; ++t) base[t * LL + static_cast<int64_t>(i) * L + j] = checked(minutes64(P, c, i, j, t), bad);
+          for (int t = 0; t < P.nt; ++t)
+            base[t * LL + static_cast<int64_t>(i) * L + j] = checked(minutes64(P, c, nullptr, i, j, t), bad);
       continue;
     }
-    __syncthreads();  // the previous instance's stage is no longer read
-    if (threadIdx.x == 0) s_mag = 0u;
+    // The previous instance's stage is no longer read, by the threads or by its bulk copy.
+    if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     __syncthreads();
+    if (L <= kSmallLoc && nt * LL + 3 <= kOut) {
+      small_instance<HAV>(P, sh.small, &queue[0][0], s_qn, s_mag, c, base, L, bad);
+      continue;
+    }
     for (int l = threadIdx.x; l < L; l += blockDim.x) {
       double x = c[2 * l], y = c[2 * l + 1];
       const float xh = static_cast<float>(HAV ? x * P.deg : x), yh = static_cast<float>(HAV ? y * P.deg : y);
@@ -153,6 +359,8 @@ __global__ void __launch_bounds__(kWarps * 32) travel_kernel(const __grid_consta
     }
     __syncthreads();
     const float S = __uint_as_float(s_mag);
+    __syncthreads();  // every thread has read S
+    if (threadIdx.x == 0) s_mag = 0u;
     int* q = queue[warp];
     int n = 0;  // queued entries (warp-uniform)
     for (int i = warp; i < L; i += kWarps) {
@@ -185,11 +393,9 @@ __global__ void __launch_bounds__(kWarps * 32) travel_kernel(const __grid_consta
         }
         // One entry of type t: rounded in float32 when sure, else queued for float64.
         auto emit = [&](int t, float kt, int32_t* rowt) {
-          const float t32 = __fmul_rn(d32, kt);
-          const float tol = rel * t32 + kt * magk + abs_part;
-          const float frac = t32 - floorf(t32);  // exact for 0 <= t32 < 2^22
-          const bool sure = screen && t32 >= 0.0f && t32 < 4194304.0f && fabsf(frac - 0.5f) > tol;
-          if (live && sure) rowt[j] = static_cast<int32_t>(rintf(t32));
+          int32_t v;
+          const bool sure = round_screened(__fmul_rn(d32, kt), rel, kt * magk + abs_part, v) && screen;
+          if (live && sure) rowt[j] = v;
           const unsigned need = __ballot_sync(0xffffffffu, live && !sure);
           if (need) {
             if (n + 32 > kQueue) {
@@ -200,31 +406,13 @@ __global__ void __launch_bounds__(kWarps * 32) travel_kernel(const __grid_consta
             n += __popc(need);
           }
         };
-        if (HAV) {  // (this loop, written out, measured faster here than through emit)
-          for (int t = 0; t < P.nt; ++t) {
-            const float t32 = __fmul_rn(d32, P.k32[t]);
-            const float tol = rel * t32 + P.k32[t] * magk + abs_part;
-            const float frac = t32 - floorf(t32);  // exact for 0 <= t32 < 2^22
-            const bool sure = screen && t32 >= 0.0f && t32 < 4194304.0f && fabsf(frac - 0.5f) > tol;
-            if (live && sure) row[t * LL + j] = static_cast<int32_t>(rintf(t32));
-            const unsigned need = __ballot_sync(0xffffffffu, live && !sure);
-            if (need) {
-              if (n + 32 > kQueue) {
-                drain(P, c, base, L, LL, q, n, lane, bad);
-                n = 0;
-              }
-              if (live && !sure) q[n + __popc(need & ((1u << lane) - 1u))] = (i << 12) | (j << 1) | t;
-              n += __popc(need);
-            }
-          }
-        } else {  // constant indices keep both types' constants in registers
-          emit(0, k0, row);
-          if (nt > 1) emit(1, k1, row1);
-        }
+        emit(0, k0, row);
+        if (nt > 1) emit(1, k1, row1);
       }
     }
     drain(P, c, base, L, LL, q, n, lane, bad);
   }
+  if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // the last bulk copy is complete
   if (bad && P.status) atomicExch(P.status, ASCHED_E_INVALID);
 }
 
@@ -274,9 +462,9 @@ extern "C" int asched_travel_matrix(const asched_travel_spec* spec, int32_t* tra
   const int64_t cap = static_cast<int64_t>(sms) * 4;  // up to 4 CTAs of 256 threads per SM
   const int grid = static_cast<int>(B < cap ? B : cap);
   if (q.metric == ASCHED_METRIC_HAVERSINE)
-    travel_kernel<true><<<grid, kWarps * 32, 0, st>>>(q);
+    travel_kernel<true><<<grid, kThreads, 0, st>>>(q);
   else
-    travel_kernel<false><<<grid, kWarps * 32, 0, st>>>(q);
+    travel_kernel<false><<<grid, kThreads, 0, st>>>(q);
   if (cudaGetLastError() != cudaSuccess) return ASCHED_E_CUDA;
   return ASCHED_OK;
 }

@@ -32,27 +32,82 @@ def test_euclidean_bit_exact_on_the_workloads():
         np.testing.assert_array_equal(bp.travel[t0:t0 + L * L].cpu().numpy().reshape(1, L, L), o)
 
 
-def test_euclidean_two_layers_and_ragged_sizes():
-    rng = np.random.default_rng(2)
-    sizes = [1, 2, 31, 32, 33, 64, 95, 300]
-    coords = [rng.uniform(-500.0, 2500.0, size=(L, 2)) for L in sizes]
+def _batch_of(coords, nt):
+    """A batch whose instance b has the locations coords[b] (matrices zeroed)."""
     insts = []
     for c in coords:
         L = len(c)
-        inst = gen.random_instance(1, n_loc=max(L, 2), n_vehicles=1, n_missions=0, n_types=2)
-        inst.travel = np.zeros((2, L, L), np.int32)
+        inst = gen.random_instance(1, n_loc=max(L, 2), n_vehicles=1, n_missions=0, n_types=nt)
+        inst.travel = np.zeros((nt, L, L), np.int32)
         inst.veh_base = np.zeros(1, np.int32)
         inst.coords = c
         insts.append(inst)
-    bp = api.BatchProblem(insts)
-    status = api.travel_into_batch(bp, _coords_tensor(insts), [300.0, 500.0])
+    return api.BatchProblem(insts), insts
+
+
+def _check_batch(coords, speeds, metric, exact=True):
+    """Build the batch's matrices on the device and compare them with the oracle's
+    (metric: the oracle's travel.EUCLIDEAN or travel.HAVERSINE)."""
+    bp, insts = _batch_of(coords, len(speeds))
+    bp.travel.fill_(-7)  # every entry must be written
+    api_metric = api.METRIC_HAVERSINE if metric == travel.HAVERSINE else api.METRIC_EUCLIDEAN
+    status = api.travel_into_batch(bp, _coords_tensor(insts), speeds, api_metric)
     torch.cuda.synchronize()
     assert int(status.item()) == api.OK
+    nt = len(speeds)
     for b, c in enumerate(coords):
         L = len(c)
         t0 = int(bp.h_travel_off[b])
-        got = bp.travel[t0:t0 + 2 * L * L].cpu().numpy().reshape(2, L, L)
-        np.testing.assert_array_equal(got, travel.travel_minutes(c, [300.0, 500.0], travel.EUCLIDEAN))
+        got = bp.travel[t0:t0 + nt * L * L].cpu().numpy().reshape(nt, L, L)
+        want = travel.travel_minutes(c, speeds, metric)
+        if exact:
+            np.testing.assert_array_equal(got, want)
+        else:  # Haversine: exact away from half minutes, else within 1
+            raw = travel.minutes_unrounded(c, speeds, metric)
+            near_half = np.abs(np.abs(raw - np.floor(raw)) - 0.5) < 1e-6
+            assert np.array_equal(got[~near_half], want[~near_half])
+            assert np.abs(got.astype(np.int64) - want).max() <= 1
+    return bp
+
+
+def test_euclidean_two_layers_and_ragged_sizes():
+    rng = np.random.default_rng(2)
+    sizes = [1, 2, 31, 32, 33, 64, 95, 300]
+    _check_batch([rng.uniform(-500.0, 2500.0, size=(L, 2)) for L in sizes], [300.0, 500.0], travel.EUCLIDEAN)
+
+
+@pytest.mark.parametrize("speeds", [[300.0, 500.0], [250.0]])
+def test_euclidean_every_small_size_and_alignment(speeds):
+    """Sizes around the limit of the shared-memory build (L <= 63 for two types, 90 for
+    one) and every 16-byte phase of an instance's block in the output."""
+    rng = np.random.default_rng(11)
+    lim = 63 if len(speeds) == 2 else 90
+    sizes = list(range(1, 20)) + [lim - 2, lim - 1, lim, lim + 1, lim + 2] + [int(x) for x in rng.integers(1, lim + 3, 40)]
+    coords = [rng.uniform(-800.0, 1800.0, size=(L, 2)) for L in sizes]
+    bp = _check_batch(coords, speeds, travel.EUCLIDEAN)
+    # blocks of 2 L^2 words start at even words; odd L^2 blocks reach every phase
+    phases = {0, 2} if len(speeds) == 2 else {0, 1, 2, 3}
+    assert {int(o) % 4 for o in bp.h_travel_off[:len(sizes)]} == phases
+
+
+def test_haversine_small_instances():
+    rng = np.random.default_rng(12)
+    coords = []
+    for L in [1, 2, 5, 17, 40, 52, 63, 64, 70]:
+        coords.append(np.stack([rng.uniform(42.0, 56.0, L), rng.uniform(-95.0, -74.0, L)], axis=1))
+    coords.append(np.stack([rng.uniform(-89.0, 89.0, 50), rng.uniform(-180.0, 180.0, 50)], axis=1))
+    _check_batch(coords, [300.0, 500.0], travel.HAVERSINE, exact=False)
+
+
+def test_half_minute_ties_overflow_the_float64_queue():
+    """Points 0.5 km apart on a line at 60 and 120 km/h: a quarter to a half of all times
+    are exact ties, far more than a warp's queue holds in one small instance; half to
+    even, as the float64 definition."""
+    coords = [np.stack([0.5 * np.arange(L) + 1000.0, np.zeros(L)], axis=1) for L in (63, 50, 7)]
+    bp = _check_batch(coords, [60.0, 120.0], travel.EUCLIDEAN)
+    L = 63
+    got = bp.travel[:L * L].cpu().numpy().reshape(L, L)
+    assert got[0, 1] == 0 and got[0, 3] == 2 and got[0, 5] == 2 and got[0, 7] == 4  # 0.5, 1.5, 2.5, 3.5 -> even
 
 
 @pytest.mark.parametrize("region", ["ontario", "globe"])
