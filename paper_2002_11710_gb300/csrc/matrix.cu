@@ -43,19 +43,22 @@
 // capacity computed where they arise.
 //
 // One CTA per instance (grid-stride over instances); the instance's coordinates are
-// staged once in shared memory (angles in radians and cos(phi) for Haversine).
-//   Small instances (n_types * L^2 + 3 <= kOut words, L <= kSmallLoc: L <= 63 for two
-//   types) are built whole in shared memory. Both distances are symmetric in every rounded
-//   operation (x_i - x_j = -(x_j - x_i) exactly, products commute), so each unordered pair
-//   i <= j is evaluated once and written to (i, j) and (j, i). The L (L + 1) / 2 pairs are
-//   numbered row by row with row i folded onto row L - 1 - i (L + 1 pairs per folded row),
-//   so the threads take consecutive numbers with no idle lanes at row ends. The finished
-//   matrices, contiguous in the output, leave by one bulk copy (cp.async.bulk, shared to
-//   global) on their 16-byte aligned middle and plain stores on the at most 3 + 3 words
-//   around it; the next instance waits only for the copy's reads of shared memory.
-//   Larger instances: warps take rows, lanes take columns, so a row's writes are
-//   contiguous. An instance with more locations than the stage holds goes through float64
-//   alone.
+// staged once in shared memory (angles in radians and cos(phi) for Haversine). Two
+// kernels share a batch, each skipping the other's instances:
+//   Small instances (n_types * L^2 + 3 <= kOut words, L <= kSmallLoc: L <= 55 for two
+//   types, 64 for one) are built whole in shared memory by 128-thread CTAs, eight per SM.
+//   Both distances are symmetric in every rounded operation (x_i - x_j = -(x_j - x_i)
+//   exactly, products commute), so each unordered pair i <= j is evaluated once and
+//   written to (i, j) and (j, i). The L (L + 1) / 2 pairs are numbered row by row with row
+//   i folded onto row L - 1 - i (L + 1 pairs per folded row), so the threads take
+//   consecutive numbers with no idle lanes at row ends. The finished matrices, contiguous
+//   in the output, leave by one bulk copy (cp.async.bulk, shared to global) on their
+//   16-byte aligned middle and plain stores on the at most 3 + 3 words around it; the
+//   next instance is staged while that copy runs and waits only for its reads of shared
+//   memory, before its first write of the matrix.
+//   Larger instances: 256-thread CTAs, warps take rows, lanes take columns, so a row's
+//   writes are contiguous. An instance with more locations than the stage holds goes
+//   through float64 alone.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -64,13 +67,18 @@
 
 namespace {
 
-constexpr int kStageLocations = 2048;  // 5 floats per location: 40 KB of shared memory
-constexpr int kSmallLoc = 96;          // locations of an instance built in shared memory
-constexpr int kOut = 8192;             // int32 words of that instance's matrices
-constexpr int kWarps = 8;
+constexpr int kStageLocations = 2048;  // large instances: 5 floats per location, 40 KB of shared memory
+constexpr int kWarps = 8;              // large-instance CTAs: 8 warps, 4 per SM
 constexpr int kThreads = kWarps * 32;
-constexpr int kQueue = 128;  // deferred float64 entries per warp
-constexpr int kCtaQueue = kWarps * kQueue;  // the same words as one queue per CTA (small instances)
+constexpr int kQueue = 128;            // deferred float64 entries per warp (large instances)
+constexpr int kSmallThreads = 128;     // small-instance CTAs: 4 warps, 8 per SM
+constexpr int kSmallLoc = 64;          // locations of an instance built in shared memory
+constexpr int kOut = 6144;             // int32 words of that instance's matrices
+constexpr int kSmallQueue = 256;       // deferred float64 entries per CTA (small instances)
+
+__host__ __device__ __forceinline__ bool is_small(int L, int nt) {
+  return L <= kSmallLoc && nt * L * L + 3 <= kOut;
+}
 
 struct MParams {
   int32_t B, nt, metric;
@@ -89,16 +97,11 @@ struct Stage {  // structure of arrays: hi and lo of both coordinates, cos(phi)
   float cphi[kStageLocations];
 };
 
-struct SmallStage {
-  float4 hl[kSmallLoc];       // (x hi, y hi, x lo, y lo)
-  float cphi[kSmallLoc];      // float(cos(phi))
-  double cos64[kSmallLoc];    // cos(phi) in float64, as the definition computes it
-  int32_t out[kOut];          // the instance's matrices, offset so that they share the output's 16-byte phase
-};
-
-union SharedStage {
-  Stage big;
-  SmallStage small;
+struct SmallStage {  // 26,368 bytes: with the queue, eight CTAs fit one SM
+  float4 hl[kSmallLoc];     // (x hi, y hi, x lo, y lo)
+  float cphi[kSmallLoc];    // float(cos(phi))
+  double cos64[kSmallLoc];  // cos(phi) in float64, as the definition computes it
+  int32_t out[kOut];        // the instance's matrices, offset so that they share the output's 16-byte phase
 };
 
 __device__ __forceinline__ double euclid(double xi, double yi, double xj, double yj) {
@@ -189,141 +192,167 @@ __device__ __forceinline__ void enqueue(bool mine, int i, int j, int t, int* cq,
   if (!mine) return;
   const unsigned pos = base + __popc(m & ((1u << lane) - 1u));
   const int e = (i << 12) | (j << 1) | t;
-  if (pos < kCtaQueue)
+  if (pos < kSmallQueue)
     cq[pos] = e;
   else
     resolve_small(P, c, cos64, o, L, e, bad);
 }
 
-// A small instance, built whole in shared memory and written out by one bulk copy.
+// Small instances, each built whole in shared memory and written out by one bulk copy.
+// The instance's scalars (S and the queue's length) alternate between two slots, so that
+// thread 0 can clear the next instance's while this one's are read.
 template <bool HAV>
-__device__ __forceinline__ void small_instance(const MParams& P, SmallStage& st, int* cq, unsigned& s_qn,
-                                               unsigned& s_mag, const double* c, int32_t* dst, int L, int& bad) {
+__global__ void __launch_bounds__(kSmallThreads, 8) travel_small_kernel(const __grid_constant__ MParams P) {
+  __shared__ __align__(16) SmallStage st;
+  __shared__ int cq[kSmallQueue];
+  __shared__ unsigned s_mag[2], s_qn[2];
   const int lane = threadIdx.x & 31;
   const int nt = P.nt;
-  for (int l = threadIdx.x; l < L; l += kThreads) {
-    double x = c[2 * l], y = c[2 * l + 1];
-    if (HAV) {
-      x *= P.deg;
-      y *= P.deg;
-    }
-    const float xh = static_cast<float>(x), yh = static_cast<float>(y);
-    if (HAV) {
-      const double cx = cos(x);
-      st.cos64[l] = cx;
-      st.cphi[l] = static_cast<float>(cx);
-      st.hl[l] = make_float4(xh, yh, static_cast<float>(x - static_cast<double>(xh)),
-                             static_cast<float>(y - static_cast<double>(yh)));
-    } else {
-      st.hl[l] = make_float4(xh, yh, 0.0f, 0.0f);
-      atomicMax(&s_mag, __float_as_uint(fabsf(xh) + fabsf(yh)));  // NaN's bits exceed every finite value
-    }
-  }
-  __syncthreads();
-  const int phase = static_cast<int>((reinterpret_cast<uintptr_t>(dst) >> 2) & 3u);
-  int32_t* o = st.out + phase;  // o[w] is dst[w]; both 16-byte aligned at the same w
-  const int LL = L * L;
   const float k0 = P.k32[0], k1 = P.k32[1];
-  float c0, c1;  // the absolute part of each type's tolerance
-  const float rel = HAV ? 8e-6f : 2e-6f;
   const float two_r32 = static_cast<float>(P.two_r);
-  if (!HAV) {
-    const float magk = 9.536743e-7f * __uint_as_float(s_mag);  // 2^-20 S
-    c0 = k0 * magk + 1e-6f;
-    c1 = k1 * magk + 1e-6f;
-  }
-  // Pair p = f (L + 1) + k: row f from column f (k < L - f), else row L - 1 - f from column k - 1.
-  const int L1 = L + 1, E = L * L1 / 2;
-  int f = threadIdx.x / L1, k = threadIdx.x - f * L1;
-  const int df = kThreads / L1, dk = kThreads - df * L1;
-  for (int p0 = 0; p0 < E; p0 += kThreads) {
-    const bool live = p0 + static_cast<int>(threadIdx.x) < E;
-    int i = f, j = f + k;
-    if (k >= L - f) {
-      i = L - 1 - f;
-      j = k - 1;
-    }
-    if (!live) i = j = 0;
-    f += df;
-    k += dk;
-    if (k >= L1) {
-      k -= L1;
-      ++f;
-    }
-    const float4 a = st.hl[i], b = st.hl[j];
-    float d32;
-    bool screen = true;
-    if (HAV) {
-      const float dx = __fadd_rn(__fsub_rn(a.x, b.x), __fsub_rn(a.z, b.z));
-      const float dy = __fadd_rn(__fsub_rn(a.y, b.y), __fsub_rn(a.w, b.w));
-      const float s1 = sinf(__fmul_rn(dx, 0.5f)), s2 = sinf(__fmul_rn(dy, 0.5f));
-      const float h = __fadd_rn(__fmul_rn(s1, s1), __fmul_rn(__fmul_rn(st.cphi[i], st.cphi[j]), __fmul_rn(s2, s2)));
-      const float r = __fsqrt_rn(h);
-      screen = r <= 0.9f;
-      d32 = __fmul_rn(two_r32, asinf(r));
-      const float magk = two_r32 * 9.094947e-13f *  // 2 r 2^-40 (sum of |angles|)
-                         (fabsf(a.x) + fabsf(b.x) + fabsf(a.y) + fabsf(b.y));
-      c0 = k0 * magk + 1e-5f;
-      c1 = k1 * magk + 1e-5f;
-    } else {
-      const float dx = __fsub_rn(a.x, b.x), dy = __fsub_rn(a.y, b.y);
-      const float q = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-      d32 = q > 0.0f ? __fmul_rn(q, rsqrtf(q)) : q;  // sqrt(0) = 0 exactly; NaN stays NaN
-    }
-    int32_t v0, v1 = 0;
-    const bool sure0 = round_screened(__fmul_rn(d32, k0), rel, c0, v0) && screen;
-    const bool sure1 = nt < 2 || (round_screened(__fmul_rn(d32, k1), rel, c1, v1) && screen);
-    if (live && sure0) {
-      o[i * L + j] = v0;
-      o[j * L + i] = v0;
-    }
-    if (live && sure1 && nt > 1) {
-      o[LL + i * L + j] = v1;
-      o[LL + j * L + i] = v1;
-    }
-    if (__ballot_sync(0xffffffffu, live && !(sure0 && sure1))) {  // rare: float64 for these
-      enqueue(live && !sure0, i, j, 0, cq, s_qn, lane, P, c, st.cos64, o, L, bad);
-      if (nt > 1) enqueue(live && !sure1, i, j, 1, cq, s_qn, lane, P, c, st.cos64, o, L, bad);
-    }
-  }
-  __syncthreads();  // the queue is complete
-  const int nq = min(static_cast<int>(s_qn), kCtaQueue);
-  for (int e = threadIdx.x; e < nq; e += kThreads) resolve_small(P, c, st.cos64, o, L, cq[e], bad);
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the writes above, before the bulk copy reads them
+  const float rel = HAV ? 8e-6f : 2e-6f;
+  int bad = 0;
+  if (threadIdx.x < 2) s_mag[threadIdx.x] = s_qn[threadIdx.x] = 0u;
   __syncthreads();
-  const int W = nt * LL;
-  const int head = min((4 - phase) & 3, W);
-  const int mid = (W - head) & ~3;
-  if (threadIdx.x == 0) {
-    if (mid > 0) {
+  int par = 0;
+  for (int b = blockIdx.x; b < P.B; b += gridDim.x) {
+    const int lo = P.loc_off[b];
+    const int L = P.loc_off[b + 1] - lo;
+    if (!is_small(L, nt)) continue;
+    const double* c = P.coords + 2 * static_cast<int64_t>(lo);
+    int32_t* dst = P.travel + P.travel_off[b];
+    // Every thread is past the previous instance's last barrier: its reads of the stage and
+    // of its slots are done.
+    if (threadIdx.x == 0) s_mag[par ^ 1] = s_qn[par ^ 1] = 0u;
+    {
+      const int l = threadIdx.x;  // L <= kSmallLoc <= kSmallThreads
+      unsigned m = 0u;
+      if (l < L) {
+        double x = c[2 * l], y = c[2 * l + 1];
+        if (HAV) {
+          x *= P.deg;
+          y *= P.deg;
+        }
+        const float xh = static_cast<float>(x), yh = static_cast<float>(y);
+        if (HAV) {
+          const double cx = cos(x);
+          st.cos64[l] = cx;
+          st.cphi[l] = static_cast<float>(cx);
+          st.hl[l] = make_float4(xh, yh, static_cast<float>(x - static_cast<double>(xh)),
+                                 static_cast<float>(y - static_cast<double>(yh)));
+        } else {
+          st.hl[l] = make_float4(xh, yh, 0.0f, 0.0f);
+          m = __float_as_uint(fabsf(xh) + fabsf(yh));  // NaN's bits exceed every finite value
+        }
+      }
+      if (!HAV) {
+        m = __reduce_max_sync(0xffffffffu, m);
+        if (lane == 0 && m) atomicMax(&s_mag[par], m);
+      }
+    }
+    if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // the last copy has read out
+    __syncthreads();
+    const int phase = static_cast<int>((reinterpret_cast<uintptr_t>(dst) >> 2) & 3u);
+    int32_t* o = st.out + phase;  // o[w] is dst[w]; both 16-byte aligned at the same w
+    const int LL = L * L;
+    float c0, c1;  // the absolute part of each type's tolerance
+    if (!HAV) {
+      const float magk = 9.536743e-7f * __uint_as_float(s_mag[par]);  // 2^-20 S
+      c0 = k0 * magk + 1e-6f;
+      c1 = k1 * magk + 1e-6f;
+    }
+    // Pair p = f (L + 1) + k: row f from column f (k < L - f), else row L - 1 - f from column k - 1.
+    const int L1 = L + 1, E = L * L1 / 2;
+    int f = threadIdx.x / L1, k = threadIdx.x - f * L1;
+    const int df = kSmallThreads / L1, dk = kSmallThreads - df * L1;
+    for (int p0 = 0; p0 < E; p0 += kSmallThreads) {
+      const bool live = p0 + static_cast<int>(threadIdx.x) < E;
+      int i = f, j = f + k;
+      if (k >= L - f) {
+        i = L - 1 - f;
+        j = k - 1;
+      }
+      if (!live) i = j = 0;
+      f += df;
+      k += dk;
+      if (k >= L1) {
+        k -= L1;
+        ++f;
+      }
+      const float4 a = st.hl[i], bb = st.hl[j];
+      float d32;
+      bool screen = true;
+      if (HAV) {
+        const float dx = __fadd_rn(__fsub_rn(a.x, bb.x), __fsub_rn(a.z, bb.z));
+        const float dy = __fadd_rn(__fsub_rn(a.y, bb.y), __fsub_rn(a.w, bb.w));
+        const float s1 = sinf(__fmul_rn(dx, 0.5f)), s2 = sinf(__fmul_rn(dy, 0.5f));
+        const float h = __fadd_rn(__fmul_rn(s1, s1), __fmul_rn(__fmul_rn(st.cphi[i], st.cphi[j]), __fmul_rn(s2, s2)));
+        const float r = __fsqrt_rn(h);
+        screen = r <= 0.9f;
+        d32 = __fmul_rn(two_r32, asinf(r));
+        const float magk = two_r32 * 9.094947e-13f *  // 2 r 2^-40 (sum of |angles|)
+                           (fabsf(a.x) + fabsf(bb.x) + fabsf(a.y) + fabsf(bb.y));
+        c0 = k0 * magk + 1e-5f;
+        c1 = k1 * magk + 1e-5f;
+      } else {
+        const float dx = __fsub_rn(a.x, bb.x), dy = __fsub_rn(a.y, bb.y);
+        const float q = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+        d32 = q > 0.0f ? __fmul_rn(q, rsqrtf(q)) : q;  // sqrt(0) = 0 exactly; NaN stays NaN
+      }
+      int32_t v0, v1 = 0;
+      const bool sure0 = round_screened(__fmul_rn(d32, k0), rel, c0, v0) && screen;
+      const bool sure1 = nt < 2 || (round_screened(__fmul_rn(d32, k1), rel, c1, v1) && screen);
+      if (live && sure0) {
+        o[i * L + j] = v0;
+        o[j * L + i] = v0;
+      }
+      if (live && sure1 && nt > 1) {
+        o[LL + i * L + j] = v1;
+        o[LL + j * L + i] = v1;
+      }
+      if (__ballot_sync(0xffffffffu, live && !(sure0 && sure1))) {  // rare: float64 for these
+        enqueue(live && !sure0, i, j, 0, cq, s_qn[par], lane, P, c, st.cos64, o, L, bad);
+        if (nt > 1) enqueue(live && !sure1, i, j, 1, cq, s_qn[par], lane, P, c, st.cos64, o, L, bad);
+      }
+    }
+    __syncthreads();  // the queue is complete
+    const int nq = min(static_cast<int>(s_qn[par]), kSmallQueue);
+    for (int e = threadIdx.x; e < nq; e += kSmallThreads) resolve_small(P, c, st.cos64, o, L, cq[e], bad);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the writes above, before the bulk copy reads them
+    __syncthreads();
+    const int W = nt * LL;
+    const int head = min((4 - phase) & 3, W);
+    const int mid = (W - head) & ~3;
+    if (threadIdx.x == 0 && mid > 0) {
       asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst + head),
                    "r"(smem_addr(o + head)), "r"(static_cast<uint32_t>(mid) * 4u)
                    : "memory");
       asm volatile("cp.async.bulk.commit_group;" ::: "memory");
     }
-    s_mag = 0u;  // every thread has read it and the queue's length
-    s_qn = 0u;
+    if (threadIdx.x < head) dst[threadIdx.x] = o[threadIdx.x];
+    const int w = head + mid + static_cast<int>(threadIdx.x);
+    if (w < W) dst[w] = o[w];
+    par ^= 1;
   }
-  if (threadIdx.x < head) dst[threadIdx.x] = o[threadIdx.x];
-  const int w = head + mid + static_cast<int>(threadIdx.x);
-  if (w < W) dst[w] = o[w];
+  if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // the last bulk copy is complete
+  if (bad && P.status) atomicExch(P.status, ASCHED_E_INVALID);
 }
 
+// Instances that are not small: warps take rows, lanes take columns.
 template <bool HAV>
 __global__ void __launch_bounds__(kThreads, 4) travel_kernel(const __grid_constant__ MParams P) {
-  __shared__ __align__(16) SharedStage sh;
+  __shared__ Stage st;
   __shared__ int queue[kWarps][kQueue];
-  __shared__ unsigned s_mag, s_qn;
-  Stage& st = sh.big;
+  __shared__ unsigned s_mag;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float two_r32 = static_cast<float>(P.two_r);
   const float k0 = P.k32[0], k1 = P.k32[1];
   const int nt = P.nt;
   int bad = 0;
-  if (threadIdx.x == 0) s_mag = s_qn = 0u;
   for (int b = blockIdx.x; b < P.B; b += gridDim.x) {
     const int lo = P.loc_off[b];
     const int L = P.loc_off[b + 1] - lo;
+    if (is_small(L, nt)) continue;
     const double* c = P.coords + 2 * static_cast<int64_t>(lo);
     int32_t* base = P.travel + P.travel_off[b];
     const int64_t LL = static_cast<int64_t>(L) * L;
@@ -334,13 +363,9 @@ __global__ void __launch_bounds__(kThreads, 4) travel_kernel(const __grid_consta
             base[t * LL + static_cast<int64_t>(i) * L + j] = checked(minutes64(P, c, nullptr, i, j, t), bad);
       continue;
     }
-    // The previous instance's stage is no longer read, by the threads or by its bulk copy.
-    if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    __syncthreads();  // the previous instance's stage is no longer read
+    if (threadIdx.x == 0) s_mag = 0u;
     __syncthreads();
-    if (L <= kSmallLoc && nt * LL + 3 <= kOut) {
-      small_instance<HAV>(P, sh.small, &queue[0][0], s_qn, s_mag, c, base, L, bad);
-      continue;
-    }
     for (int l = threadIdx.x; l < L; l += blockDim.x) {
       double x = c[2 * l], y = c[2 * l + 1];
       const float xh = static_cast<float>(HAV ? x * P.deg : x), yh = static_cast<float>(HAV ? y * P.deg : y);
@@ -359,8 +384,6 @@ __global__ void __launch_bounds__(kThreads, 4) travel_kernel(const __grid_consta
     }
     __syncthreads();
     const float S = __uint_as_float(s_mag);
-    __syncthreads();  // every thread has read S
-    if (threadIdx.x == 0) s_mag = 0u;
     int* q = queue[warp];
     int n = 0;  // queued entries (warp-uniform)
     for (int i = warp; i < L; i += kWarps) {
@@ -412,7 +435,6 @@ __global__ void __launch_bounds__(kThreads, 4) travel_kernel(const __grid_consta
     }
     drain(P, c, base, L, LL, q, n, lane, bad);
   }
-  if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // the last bulk copy is complete
   if (bad && P.status) atomicExch(P.status, ASCHED_E_INVALID);
 }
 
@@ -459,12 +481,39 @@ extern "C" int asched_travel_matrix(const asched_travel_spec* spec, int32_t* tra
     (void)cudaGetLastError();
     return ASCHED_E_CUDA;
   }
-  const int64_t cap = static_cast<int64_t>(sms) * 4;  // up to 4 CTAs of 256 threads per SM
-  const int grid = static_cast<int>(B < cap ? B : cap);
-  if (q.metric == ASCHED_METRIC_HAVERSINE)
-    travel_kernel<true><<<grid, kThreads, 0, st>>>(q);
-  else
-    travel_kernel<false><<<grid, kThreads, 0, st>>>(q);
-  if (cudaGetLastError() != cudaSuccess) return ASCHED_E_CUDA;
+  int64_t n_small = 0;
+  for (int b = 0; b < B; ++b) n_small += is_small(spec->h_loc_off[b + 1] - spec->h_loc_off[b], q.nt);
+  const bool hav = q.metric == ASCHED_METRIC_HAVERSINE;
+  if (n_small > 0) {
+    static bool carveout_set[2] = {false, false};  // eight 27 KB CTAs per SM want the largest shared-memory carveout
+    if (!carveout_set[hav]) {
+      const cudaError_t e =
+          hav ? cudaFuncSetAttribute(travel_small_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared)
+              : cudaFuncSetAttribute(travel_small_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared);
+      if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return ASCHED_E_CUDA;
+      }
+      carveout_set[hav] = true;
+    }
+    const int64_t cap = static_cast<int64_t>(sms) * 8;  // 8 CTAs of 128 threads per SM
+    const int grid = static_cast<int>(n_small < cap ? n_small : cap);
+    if (hav)
+      travel_small_kernel<true><<<grid, kSmallThreads, 0, st>>>(q);
+    else
+      travel_small_kernel<false><<<grid, kSmallThreads, 0, st>>>(q);
+    if (cudaGetLastError() != cudaSuccess) return ASCHED_E_CUDA;
+  }
+  if (n_small < B) {
+    const int64_t cap = static_cast<int64_t>(sms) * 4;  // 4 CTAs of 256 threads per SM
+    const int grid = static_cast<int>(B - n_small < cap ? B - n_small : cap);
+    if (hav)
+      travel_kernel<true><<<grid, kThreads, 0, st>>>(q);
+    else
+      travel_kernel<false><<<grid, kThreads, 0, st>>>(q);
+    if (cudaGetLastError() != cudaSuccess) return ASCHED_E_CUDA;
+  }
   return ASCHED_OK;
 }

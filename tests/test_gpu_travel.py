@@ -78,10 +78,10 @@ def test_euclidean_two_layers_and_ragged_sizes():
 
 @pytest.mark.parametrize("speeds", [[300.0, 500.0], [250.0]])
 def test_euclidean_every_small_size_and_alignment(speeds):
-    """Sizes around the limit of the shared-memory build (L <= 63 for two types, 90 for
+    """Sizes around the limit of the shared-memory build (L <= 55 for two types, 64 for
     one) and every 16-byte phase of an instance's block in the output."""
     rng = np.random.default_rng(11)
-    lim = 63 if len(speeds) == 2 else 90
+    lim = 55 if len(speeds) == 2 else 64
     sizes = list(range(1, 20)) + [lim - 2, lim - 1, lim, lim + 1, lim + 2] + [int(x) for x in rng.integers(1, lim + 3, 40)]
     coords = [rng.uniform(-800.0, 1800.0, size=(L, 2)) for L in sizes]
     bp = _check_batch(coords, speeds, travel.EUCLIDEAN)
@@ -93,7 +93,7 @@ def test_euclidean_every_small_size_and_alignment(speeds):
 def test_haversine_small_instances():
     rng = np.random.default_rng(12)
     coords = []
-    for L in [1, 2, 5, 17, 40, 52, 63, 64, 70]:
+    for L in [1, 2, 5, 17, 40, 52, 55, 56, 64, 70]:
         coords.append(np.stack([rng.uniform(42.0, 56.0, L), rng.uniform(-95.0, -74.0, L)], axis=1))
     coords.append(np.stack([rng.uniform(-89.0, 89.0, 50), rng.uniform(-180.0, 180.0, 50)], axis=1))
     _check_batch(coords, [300.0, 500.0], travel.HAVERSINE, exact=False)
@@ -101,11 +101,11 @@ def test_haversine_small_instances():
 
 def test_half_minute_ties_overflow_the_float64_queue():
     """Points 0.5 km apart on a line at 60 and 120 km/h: a quarter to a half of all times
-    are exact ties, far more than a warp's queue holds in one small instance; half to
-    even, as the float64 definition."""
-    coords = [np.stack([0.5 * np.arange(L) + 1000.0, np.zeros(L)], axis=1) for L in (63, 50, 7)]
+    are exact ties, far more than the float64 queue of a small instance holds (and a
+    large instance beside them); half to even, as the float64 definition."""
+    coords = [np.stack([0.5 * np.arange(L) + 1000.0, np.zeros(L)], axis=1) for L in (55, 50, 7, 63)]
     bp = _check_batch(coords, [60.0, 120.0], travel.EUCLIDEAN)
-    L = 63
+    L = 55
     got = bp.travel[:L * L].cpu().numpy().reshape(L, L)
     assert got[0, 1] == 0 and got[0, 3] == 2 and got[0, 5] == 2 and got[0, 7] == 4  # 0.5, 1.5, 2.5, 3.5 -> even
 
