@@ -30,7 +30,9 @@
 //              number below 1.9 for sqrt(a) <= 0.9 (larger values go to float64 outright)
 //              add below 1.8e-6 relative; screened at 8e-6 t + (60 / speed) 2 r 2^-40
 //              (sum of |angles|) + 1e-5.
-// Times of 2^22 minutes or more also go to float64. The float32 time is rounded by adding
+// Times of 2^22 minutes or more also go to float64 (small instances: every entry of an
+// instance whose largest possible time, 2 S * 60 / speed or pi r * 60 / speed, is not
+// below 2^22, through an infinite tolerance). The float32 time is rounded by adding
 // and subtracting 1.5 * 2^23: for 0 <= t < 2^22 the sum lies in [2^23, 2^24), where the
 // float32 spacing is 1, so the addition itself rounds t half to even, the integer is the
 // sum's low mantissa bits, and t minus the rounded value is exact (Sterbenz), which gives
@@ -84,6 +86,7 @@ struct MParams {
   int32_t B, nt, metric;
   double speed[2];
   float k32[2];  // float(60 / speed)
+  float rel_hav;  // Haversine screen: 8e-6, or infinity if a time may reach 2^22 minutes
   double two_r, deg;
   const int32_t* loc_off;
   const int64_t* travel_off;
@@ -151,6 +154,14 @@ __device__ __forceinline__ bool round_screened(float t32, float rel, float c, in
   return t32 < 4194304.0f && gap > __fmaf_rn(rel, t32, c);
 }
 
+// The same where t32 < 2^22 is known or rel is infinite (every comparison then fails).
+__device__ __forceinline__ bool round_screened_bounded(float t32, float rel, float c, int32_t& v) {
+  const float s = __fadd_rn(t32, 12582912.0f);
+  const float gap = __fsub_rn(0.5f, fabsf(__fsub_rn(t32, __fsub_rn(s, 12582912.0f))));
+  v = __float_as_int(s) - 0x4B400000;
+  return gap > __fmaf_rn(rel, t32, c);
+}
+
 // Drain a warp's queue of deferred entries into the output rows: each lane takes entries
 // and writes the float64 result.
 __device__ __forceinline__ void drain(const MParams& P, const double* c, int32_t* base, int L, int64_t LL,
@@ -200,17 +211,18 @@ __device__ __forceinline__ void enqueue(bool mine, int i, int j, int t, int* cq,
 
 // Small instances, each built whole in shared memory and written out by one bulk copy.
 // The instance's scalars (S and the queue's length) alternate between two slots, so that
-// thread 0 can clear the next instance's while this one's are read.
-template <bool HAV>
+// thread 0 can clear the next instance's while this one's are read. Every evaluated pair
+// stores its float32 results; the float64 drain after the queue barrier overwrites the
+// uncertain ones. NT: the number of vehicle types.
+template <bool HAV, int NT>
 __global__ void __launch_bounds__(kSmallThreads, 8) travel_small_kernel(const __grid_constant__ MParams P) {
   __shared__ __align__(16) SmallStage st;
   __shared__ int cq[kSmallQueue];
   __shared__ unsigned s_mag[2], s_qn[2];
   const int lane = threadIdx.x & 31;
-  const int nt = P.nt;
+  const int nt = NT;
   const float k0 = P.k32[0], k1 = P.k32[1];
   const float two_r32 = static_cast<float>(P.two_r);
-  const float rel = HAV ? 8e-6f : 2e-6f;
   int bad = 0;
   if (threadIdx.x < 2) s_mag[threadIdx.x] = s_qn[threadIdx.x] = 0u;
   __syncthreads();
@@ -256,10 +268,14 @@ __global__ void __launch_bounds__(kSmallThreads, 8) travel_small_kernel(const __
     int32_t* o = st.out + phase;  // o[w] is dst[w]; both 16-byte aligned at the same w
     const int LL = L * L;
     float c0, c1;  // the absolute part of each type's tolerance
+    float rel = P.rel_hav;
     if (!HAV) {
-      const float magk = 9.536743e-7f * __uint_as_float(s_mag[par]);  // 2^-20 S
+      const float S = __uint_as_float(s_mag[par]);
+      const float magk = 9.536743e-7f * S;  // 2^-20 S
       c0 = k0 * magk + 1e-6f;
       c1 = k1 * magk + 1e-6f;
+      // every time is below 2 S k (1 + 10 2^-24); false for a NaN or infinite S
+      rel = 2.0f * S * fmaxf(k0, NT > 1 ? k1 : 0.0f) * 1.001f < 4194304.0f ? 2e-6f : __int_as_float(0x7f800000);
     }
     // Pair p = f (L + 1) + k: row f from column f (k < L - f), else row L - 1 - f from column k - 1.
     const int L1 = L + 1, E = L * L1 / 2;
@@ -299,20 +315,19 @@ __global__ void __launch_bounds__(kSmallThreads, 8) travel_small_kernel(const __
         const float q = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
         d32 = q > 0.0f ? __fmul_rn(q, rsqrtf(q)) : q;  // sqrt(0) = 0 exactly; NaN stays NaN
       }
+      if (!live) d32 = 0.0f;  // so that its stores write the 0 of entry (0, 0), whatever the coordinates
       int32_t v0, v1 = 0;
-      const bool sure0 = round_screened(__fmul_rn(d32, k0), rel, c0, v0) && screen;
-      const bool sure1 = nt < 2 || (round_screened(__fmul_rn(d32, k1), rel, c1, v1) && screen);
-      if (live && sure0) {
-        o[i * L + j] = v0;
-        o[j * L + i] = v0;
-      }
-      if (live && sure1 && nt > 1) {
+      const bool sure0 = round_screened_bounded(__fmul_rn(d32, k0), rel, c0, v0) && screen;
+      const bool sure1 = NT < 2 || (round_screened_bounded(__fmul_rn(d32, k1), rel, c1, v1) && screen);
+      o[i * L + j] = v0;
+      o[j * L + i] = v0;
+      if (NT > 1) {
         o[LL + i * L + j] = v1;
         o[LL + j * L + i] = v1;
       }
       if (__ballot_sync(0xffffffffu, live && !(sure0 && sure1))) {  // rare: float64 for these
         enqueue(live && !sure0, i, j, 0, cq, s_qn[par], lane, P, c, st.cos64, o, L, bad);
-        if (nt > 1) enqueue(live && !sure1, i, j, 1, cq, s_qn[par], lane, P, c, st.cos64, o, L, bad);
+        if (NT > 1) enqueue(live && !sure1, i, j, 1, cq, s_qn[par], lane, P, c, st.cos64, o, L, bad);
       }
     }
     __syncthreads();  // the queue is complete
@@ -470,6 +485,10 @@ extern "C" int asched_travel_matrix(const asched_travel_spec* spec, int32_t* tra
   q.k32[1] = static_cast<float>(60.0 / q.speed[1]);
   const double r = spec->radius_km > 0.0 ? spec->radius_km : 6371.0;
   q.two_r = 2.0 * r;
+  {  // every Haversine time is at most pi r 60 / speed (a float32 margin of 2^-10)
+    const double kmax = 60.0 / (q.nt > 1 && q.speed[1] < q.speed[0] ? q.speed[1] : q.speed[0]);
+    q.rel_hav = 3.141592653589793 * r * kmax * (1.0 + 1.0 / 1024.0) < 4194304.0 ? 8e-6f : INFINITY;
+  }
   q.deg = 3.141592653589793 / 180.0;
   q.loc_off = spec->loc_off;
   q.travel_off = spec->travel_off;
@@ -485,25 +504,21 @@ extern "C" int asched_travel_matrix(const asched_travel_spec* spec, int32_t* tra
   for (int b = 0; b < B; ++b) n_small += is_small(spec->h_loc_off[b + 1] - spec->h_loc_off[b], q.nt);
   const bool hav = q.metric == ASCHED_METRIC_HAVERSINE;
   if (n_small > 0) {
-    static bool carveout_set[2] = {false, false};  // eight 27 KB CTAs per SM want the largest shared-memory carveout
-    if (!carveout_set[hav]) {
-      const cudaError_t e =
-          hav ? cudaFuncSetAttribute(travel_small_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     cudaSharedmemCarveoutMaxShared)
-              : cudaFuncSetAttribute(travel_small_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     cudaSharedmemCarveoutMaxShared);
-      if (e != cudaSuccess) {
+    void (*const kernels[2][2])(MParams) = {{travel_small_kernel<false, 1>, travel_small_kernel<false, 2>},
+                                            {travel_small_kernel<true, 1>, travel_small_kernel<true, 2>}};
+    void (*const kern)(MParams) = kernels[hav][q.nt - 1];
+    static bool carveout_set[2][2] = {{false, false}, {false, false}};
+    if (!carveout_set[hav][q.nt - 1]) {  // eight 27 KB CTAs per SM want the largest shared-memory carveout
+      if (cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
+          cudaSuccess) {
         (void)cudaGetLastError();
         return ASCHED_E_CUDA;
       }
-      carveout_set[hav] = true;
+      carveout_set[hav][q.nt - 1] = true;
     }
     const int64_t cap = static_cast<int64_t>(sms) * 8;  // 8 CTAs of 128 threads per SM
     const int grid = static_cast<int>(n_small < cap ? n_small : cap);
-    if (hav)
-      travel_small_kernel<true><<<grid, kSmallThreads, 0, st>>>(q);
-    else
-      travel_small_kernel<false><<<grid, kSmallThreads, 0, st>>>(q);
+    kern<<<grid, kSmallThreads, 0, st>>>(q);
     if (cudaGetLastError() != cudaSuccess) return ASCHED_E_CUDA;
   }
   if (n_small < B) {

@@ -129,6 +129,33 @@ def test_haversine_matches_the_oracle(region):
     assert (np.diagonal(got, axis1=1, axis2=2) == 0).all()
 
 
+def test_invalid_and_far_points_in_small_instances():
+    """A NaN at location 0 of a 55-location instance (every entry uncertain, far more than
+    the float64 queue holds): its entries read 0, the rest are exact, status E_INVALID.
+    Coordinates of 10^7 km (times may pass 2^22 minutes, so every entry goes through
+    float64) stay exact; other instances of the batch are untouched."""
+    rng = np.random.default_rng(13)
+    good = rng.uniform(0.0, 1000.0, (40, 2))
+    nan0 = rng.uniform(0.0, 1000.0, (55, 2))
+    nan0[0, 0] = np.nan
+    far = rng.uniform(-1e7, 1e7, (30, 2))
+    coords = [good, nan0, far]
+    bp, insts = _batch_of(coords, 2)
+    bp.travel.fill_(-7)
+    status = api.travel_into_batch(bp, _coords_tensor(insts), [300.0, 500.0], api.METRIC_EUCLIDEAN)
+    torch.cuda.synchronize()
+    assert int(status.item()) == api.E_INVALID
+    got = []
+    for b, c in enumerate(coords):
+        L = len(c)
+        t0 = int(bp.h_travel_off[b])
+        got.append(bp.travel[t0:t0 + 2 * L * L].cpu().numpy().reshape(2, L, L))
+    np.testing.assert_array_equal(got[0], travel.travel_minutes(good, [300.0, 500.0], travel.EUCLIDEAN))
+    np.testing.assert_array_equal(got[2], travel.travel_minutes(far, [300.0, 500.0], travel.EUCLIDEAN))
+    assert (got[1][:, 0, :] == 0).all() and (got[1][:, :, 0] == 0).all()
+    np.testing.assert_array_equal(got[1][:, 1:, 1:], travel.travel_minutes(nan0[1:], [300.0, 500.0], travel.EUCLIDEAN))
+
+
 def test_status_and_host_errors():
     ll = np.array([[0.0, 0.0], [np.nan, 1.0], [1.0, 1.0]])
     with pytest.raises(api.AschedError) as e:
