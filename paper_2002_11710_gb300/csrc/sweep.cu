@@ -77,12 +77,26 @@ __device__ __forceinline__ int key_delta(uint64_t key) {
   return static_cast<int>(static_cast<uint32_t>(key >> 32) ^ 0x80000000u);
 }
 
-// Least key over the block; every thread gets it. Contains one __syncthreads, so a
-// caller must separate two calls by another barrier (red is reused).
+// The block's barrier: a warp barrier when the block is one warp (W).
+template <bool W>
+__device__ __forceinline__ void bar() {
+  if (W)
+    __syncwarp();
+  else
+    __syncthreads();
+}
+
+// Least key over the block; every thread gets it. Contains one barrier, so a caller
+// must separate two calls by another barrier (red is reused).
+template <bool W>
 __device__ __forceinline__ uint64_t block_min(uint64_t key, uint64_t* red) {
   for (int o = 16; o > 0; o >>= 1) {
     const uint64_t other = __shfl_xor_sync(0xffffffffu, key, o);
     key = other < key ? other : key;
+  }
+  if (W) {
+    __syncwarp();
+    return key;
   }
   const int nw = blockDim.x >> 5;
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = key;
@@ -120,7 +134,7 @@ struct Run {
 // One step: mission j of vehicle i (candidates, break rule, tabu list and acceptance as
 // in asched.h). Every thread calls it with the same arguments (it holds barriers);
 // returns the node after j before the step, which is still on i.
-template <bool PEN, bool DL, bool TABU>
+template <bool PEN, bool DL, bool TABU, bool W>
 __device__ __forceinline__ int sweep_step(const Sw& s, int i, int j, Run& r, uint64_t* red, bool& applied) {
   const int M = s.M, V = s.V, N = s.N, cap = s.cap, lam = s.lam;
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -199,7 +213,7 @@ __device__ __forceinline__ int sweep_step(const Sw& s, int i, int j, Run& r, uin
       uint64_t key;
       if (cand(y, k, q, ins, ok, key) && !ok) atomicMin(&s.fbad[k], q);
     }
-    __syncthreads();
+    bar<W>();
     // Pass 2: the least (delta, k, q) before each vehicle's first infeasible point.
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
@@ -223,7 +237,7 @@ __device__ __forceinline__ int sweep_step(const Sw& s, int i, int j, Run& r, uin
       }
     }
   }
-  const uint64_t win = rem_ok ? block_min(best, red) : kNoKey;
+  const uint64_t win = rem_ok ? block_min<W>(best, red) : kNoKey;
   const int d = win == kNoKey ? 0 : key_delta(win);
   const bool apply = win != kNoKey && (d < 0 || r.accept_worse);
   if (apply && best == win) {
@@ -274,7 +288,7 @@ __device__ __forceinline__ int sweep_step(const Sw& s, int i, int j, Run& r, uin
       improved = true;
     }
   }
-  __syncthreads();
+  bar<W>();
   if (improved && r.keep_best)
     for (int w = tid; w < N; w += nthr) s.bnx[w] = s.nxt[w];
   ++r.step;
@@ -285,21 +299,21 @@ __device__ __forceinline__ int sweep_step(const Sw& s, int i, int j, Run& r, uin
 // as its route stands when the turn starts, in route order or by increasing rank (missions
 // only leave the vehicle during its turn, and are skipped once gone). Returns whether a
 // move was applied.
-template <bool PEN, bool DL, bool TABU>
+template <bool PEN, bool DL, bool TABU, bool W>
 __device__ __forceinline__ bool sweep_pass(const Sw& s, Run& r, uint64_t* red) {
   const int M = s.M, tid = threadIdx.x, nthr = blockDim.x;
   bool applied = false;
   for (int ii = 0; ii < s.V; ++ii) {
     const int i = s.vord[ii];
     const int n = s.nlen[i];
-    __syncthreads();  // every thread is done with the previous turn's list
+    bar<W>();  // every thread is done with the previous turn's list
     if (tid == 0) {
       int k = 0;
       for (int w = s.nxt[M + i]; w != M + i; w = s.nxt[w]) s.turn[k++] = w;
     }
     const int32_t* list = s.turn;
     if (s.ranked) {
-      __syncthreads();
+      bar<W>();
       for (int k = tid; k < n; k += nthr) {  // place each mission at its rank among the turn's
         const int m = s.turn[k], rm = s.mrk[m];
         int at = 0;
@@ -308,10 +322,10 @@ __device__ __forceinline__ bool sweep_pass(const Sw& s, Run& r, uint64_t* red) {
       }
       list = s.sorted;
     }
-    __syncthreads();
+    bar<W>();
     for (int k = 0; k < n; ++k) {
       const int j = list[k];
-      if (s.veh[j] == i) sweep_step<PEN, DL, TABU>(s, i, j, r, red, applied);
+      if (s.veh[j] == i) sweep_step<PEN, DL, TABU, W>(s, i, j, r, red, applied);
     }
   }
   return applied;
@@ -319,7 +333,7 @@ __device__ __forceinline__ bool sweep_pass(const Sw& s, Run& r, uint64_t* red) {
 
 // Algorithm 1's choice for mission m: the least (objective increase, vehicle) among the
 // vehicles it can be appended to; kNoKey when none. One thread per vehicle.
-template <bool PEN, bool DL>
+template <bool PEN, bool DL, bool W>
 __device__ __forceinline__ uint64_t greedy_pick(const Sw& s, int m, uint64_t* red) {
   const int M = s.M;
   const int w = s.wm[m];
@@ -344,7 +358,7 @@ __device__ __forceinline__ uint64_t greedy_pick(const Sw& s, int m, uint64_t* re
       key = kv < key ? kv : key;
     }
   }
-  return block_min(key, red);
+  return block_min<W>(key, red);
 }
 
 // ONE_WARP: the 32-thread launch of small instances, bounded to 64 registers so that 32
@@ -422,10 +436,24 @@ __global__ void __launch_bounds__(ONE_WARP ? 32 : kMaxThreads, ONE_WARP ? 32 : 1
     s.vord[v] = Q.vehicle_order ? Q.vehicle_order[vo + v] : v;
   }
   int maxT = 0;
-  for (int64_t x = tid; x < static_cast<int64_t>(nt) * L * L; x += nthr) {
-    const int t = __ldg(s.T + x);
-    bad |= t < 0;
-    maxT = t > maxT ? t : maxT;
+  {  // the matrices, 16 bytes per load between an unaligned head and tail
+    const int64_t n = static_cast<int64_t>(nt) * L * L;
+    const int64_t head = min(static_cast<int64_t>((16u - (reinterpret_cast<uintptr_t>(s.T) & 15u)) & 15u) / 4, n);
+    const int64_t n4 = (n - head) >> 2;
+    auto see = [&](int t) {
+      bad |= t < 0;
+      maxT = t > maxT ? t : maxT;
+    };
+    for (int64_t x = tid; x < head; x += nthr) see(__ldg(s.T + x));
+    const int4* T4 = reinterpret_cast<const int4*>(s.T + head);
+    for (int64_t x = tid; x < n4; x += nthr) {
+      const int4 t = __ldg(T4 + x);
+      see(t.x);
+      see(t.y);
+      see(t.z);
+      see(t.w);
+    }
+    for (int64_t x = head + 4 * n4 + tid; x < n; x += nthr) see(__ldg(s.T + x));
   }
   for (int o = 16; o > 0; o >>= 1) {
     const int other = __shfl_xor_sync(0xffffffffu, maxT, o);
@@ -503,12 +531,12 @@ __global__ void __launch_bounds__(ONE_WARP ? 32 : kMaxThreads, ONE_WARP ? 32 : 1
     int fail = 0;
     for (int r = 0; r < M; ++r) {
       const int m = order[r];
-      uint64_t key = greedy_pick<PEN, DL>(s, m, s_red);
+      uint64_t key = greedy_pick<PEN, DL, ONE_WARP>(s, m, s_red);
       if (key == kNoKey && Q.repair && r > 0) {
-        __syncthreads();  // s_red is read by every thread before the sweep reuses it
+        bar<ONE_WARP>();  // s_red is read by every thread before the sweep reuses it
         Run rep = {};
         rep.keep_best = false;
-        if (sweep_pass<PEN, DL, false>(s, rep, s_red)) key = greedy_pick<PEN, DL>(s, m, s_red);
+        if (sweep_pass<PEN, DL, false, ONE_WARP>(s, rep, s_red)) key = greedy_pick<PEN, DL, ONE_WARP>(s, m, s_red);
       }
       if (key == kNoKey) {
         fail = 1;
@@ -531,7 +559,7 @@ __global__ void __launch_bounds__(ONE_WARP ? 32 : kMaxThreads, ONE_WARP ? 32 : 1
         s.pos[M + v] = s.nlen[v];
         s.fl[v] += a + bret - old;
       }
-      __syncthreads();
+      bar<ONE_WARP>();
     }
     if (fail) status = ASCHED_E_INFEASIBLE_INIT;
   }
@@ -561,7 +589,7 @@ __global__ void __launch_bounds__(ONE_WARP ? 32 : kMaxThreads, ONE_WARP ? 32 : 1
     bool go_on = true;
     while (go_on && sweeps < Q.max_sweeps) {
       const int zb0 = run.z_best;
-      const bool applied = sweep_pass<PEN, DL, TABU>(s, run, s_red);
+      const bool applied = sweep_pass<PEN, DL, TABU, ONE_WARP>(s, run, s_red);
       ++sweeps;
       go_on = Q.accept_worse ? (run.z_best < zb0) : applied;
     }
