@@ -48,7 +48,7 @@
 // staged once in shared memory (angles in radians and cos(phi) for Haversine). Two
 // kernels share a batch, each skipping the other's instances:
 //   Small instances (n_types * L^2 + 3 <= kOut words, L <= kSmallLoc: L <= 55 for two
-//   types, 64 for one) are built whole in shared memory by 128-thread CTAs, eight per SM.
+//   types, 78 for one) are built whole in shared memory by 128-thread CTAs, eight per SM.
 //   Both distances are symmetric in every rounded operation (x_i - x_j = -(x_j - x_i)
 //   exactly, products commute), so each unordered pair i <= j is evaluated once and
 //   written to (i, j) and (j, i). The L (L + 1) / 2 pairs are numbered row by row with row
@@ -63,6 +63,7 @@
 //   through float64 alone.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "asched.h"
@@ -74,7 +75,7 @@ constexpr int kWarps = 8;              // large-instance CTAs: 8 warps, 4 per SM
 constexpr int kThreads = kWarps * 32;
 constexpr int kQueue = 128;            // deferred float64 entries per warp (large instances)
 constexpr int kSmallThreads = 128;     // small-instance CTAs: 4 warps, 8 per SM
-constexpr int kSmallLoc = 64;          // locations of an instance built in shared memory
+constexpr int kSmallLoc = 80;          // locations of an instance built in shared memory
 constexpr int kOut = 6144;             // int32 words of that instance's matrices
 constexpr int kSmallQueue = 256;       // deferred float64 entries per CTA (small instances)
 
@@ -100,12 +101,14 @@ struct Stage {  // structure of arrays: hi and lo of both coordinates, cos(phi)
   float cphi[kStageLocations];
 };
 
-struct SmallStage {  // 26,368 bytes: with the queue, eight CTAs fit one SM
+struct SmallStage {  // 26,816 bytes: with the queue, eight CTAs fit one SM
   float4 hl[kSmallLoc];     // (x hi, y hi, x lo, y lo)
   float cphi[kSmallLoc];    // float(cos(phi))
   double cos64[kSmallLoc];  // cos(phi) in float64, as the definition computes it
   int32_t out[kOut];        // the instance's matrices, offset so that they share the output's 16-byte phase
 };
+static_assert(offsetof(SmallStage, out) % 16 == 0, "the bulk copy reads out at 16-byte boundaries");
+static_assert(kSmallLoc <= kSmallThreads, "one location per thread when staging");
 
 __device__ __forceinline__ double euclid(double xi, double yi, double xj, double yj) {
   const double dx = __dsub_rn(xi, xj), dy = __dsub_rn(yi, yj);

@@ -78,10 +78,10 @@ def test_euclidean_two_layers_and_ragged_sizes():
 
 @pytest.mark.parametrize("speeds", [[300.0, 500.0], [250.0]])
 def test_euclidean_every_small_size_and_alignment(speeds):
-    """Sizes around the limit of the shared-memory build (L <= 55 for two types, 64 for
+    """Sizes around the limit of the shared-memory build (L <= 55 for two types, 78 for
     one) and every 16-byte phase of an instance's block in the output."""
     rng = np.random.default_rng(11)
-    lim = 55 if len(speeds) == 2 else 64
+    lim = 55 if len(speeds) == 2 else 78
     sizes = list(range(1, 20)) + [lim - 2, lim - 1, lim, lim + 1, lim + 2] + [int(x) for x in rng.integers(1, lim + 3, 40)]
     coords = [rng.uniform(-800.0, 1800.0, size=(L, 2)) for L in sizes]
     bp = _check_batch(coords, speeds, travel.EUCLIDEAN)
