@@ -510,14 +510,12 @@ extern "C" int asched_travel_matrix(const asched_travel_spec* spec, int32_t* tra
     void (*const kernels[2][2])(MParams) = {{travel_small_kernel<false, 1>, travel_small_kernel<false, 2>},
                                             {travel_small_kernel<true, 1>, travel_small_kernel<true, 2>}};
     void (*const kern)(MParams) = kernels[hav][q.nt - 1];
-    static bool carveout_set[2][2] = {{false, false}, {false, false}};
-    if (!carveout_set[hav][q.nt - 1]) {  // eight 27 KB CTAs per SM want the largest shared-memory carveout
-      if (cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
-          cudaSuccess) {
-        (void)cudaGetLastError();
-        return ASCHED_E_CUDA;
-      }
-      carveout_set[hav][q.nt - 1] = true;
+    // eight 28 KB CTAs per SM want the largest shared-memory carveout (a per-device
+    // attribute of the function, so it is set on every call: a host call, no device work)
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
+        cudaSuccess) {
+      (void)cudaGetLastError();
+      return ASCHED_E_CUDA;
     }
     const int64_t cap = static_cast<int64_t>(sms) * 8;  // 8 CTAs of 128 threads per SM
     const int grid = static_cast<int>(n_small < cap ? n_small : cap);
