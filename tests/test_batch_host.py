@@ -76,3 +76,35 @@ def test_sweep_host_argument_errors_need_no_gpu():
     empty = api.BatchProblem([], device="cpu")
     assert L.asched_sweep_batch(ctypes.byref(empty.struct), api.SWEEP_TABU, ctypes.byref(api.sweep_params(5)),
                                 None, ctypes.byref(empty.alloc_output().struct()), None, None) == api.OK
+
+
+def test_travel_host_argument_errors_need_no_gpu():
+    """asched_travel_matrix rejects bad specs on the host before any CUDA call (status
+    NULL, so nothing touches a device)."""
+    import ctypes
+
+    from paper_2002_11710_gb300 import _lib
+    L = _lib.load()
+    off = np.array([0, 3, 7], dtype=np.int32)
+    fake = ctypes.c_void_p(16)  # device pointers the host never dereferences
+    travel = ctypes.c_void_p(64)
+
+    def spec(**kw):
+        f = dict(n=2, h=off, nt=2, speeds=(300.0, 500.0), metric=api.METRIC_EUCLIDEAN, radius=0.0)
+        f.update(kw)
+        h = f["h"]
+        return _lib.TravelSpec(f["n"], ctypes.c_void_p(h.ctypes.data) if h is not None else None, fake, fake, fake,
+                               f["nt"], (ctypes.c_double * 2)(*f["speeds"]), f["metric"], f["radius"])
+
+    def call(s, out=travel):
+        return L.asched_travel_matrix(ctypes.byref(s) if s is not None else None, out, None, None)
+
+    assert call(None) == api.E_INVALID
+    assert call(spec(), out=None) == api.E_INVALID
+    for kw in (dict(n=-1), dict(nt=0), dict(nt=3), dict(metric=7), dict(speeds=(0.0, 500.0)),
+               dict(speeds=(300.0, -1.0)), dict(speeds=(float("inf"), 500.0)), dict(speeds=(float("nan"), 500.0)),
+               dict(metric=api.METRIC_HAVERSINE, radius=-1.0),
+               dict(metric=api.METRIC_HAVERSINE, radius=float("inf")), dict(h=None),
+               dict(h=np.array([1, 3, 7], dtype=np.int32)), dict(h=np.array([0, 3, 3], dtype=np.int32))):
+        assert call(spec(**kw)) == api.E_INVALID, kw
+    assert call(spec(n=0)) == api.OK  # nothing to build
