@@ -54,6 +54,28 @@ def _env_int(k, d):
         return d
 
 
+TIMING_BACK_TO_BACK = "device time per call: 5 calls back to back between CUDA events, median of 3 such runs"
+
+
+def device_ms(fn, reps=5, rounds=3):
+    """Device time per call of fn (which queues work on the current stream): reps calls
+    back to back between two CUDA events, so the host queues ahead and its own time per
+    call (argument checks, Python) does not leave the device idle; median over rounds."""
+    import torch
+
+    ts = []
+    for _ in range(rounds):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b) / reps)
+    return statistics.median(ts)
+
+
 def traffic_bytes():
     src = os.path.join(ROOT, "paper_2002_11710_gb300", "csrc", "asched.cu")
     with open(src, "rb") as f:
@@ -440,21 +462,13 @@ def run_travel_matrix(args, bp, insts, dev):
     pairs = int((L * L).sum())
     nbytes = 4 * bp.n_types * pairs + 16 * int(L.sum())
     res = {"workload": f"{bp.B:,} instances, {pairs:,} location pairs, 2 layers (300 / 500 km/h)",
-           "bytes_per_launch": nbytes, "gpu_launches": 1}
+           "bytes_per_launch": nbytes, "gpu_launches": 1, "timing": TIMING_BACK_TO_BACK}
     for name, c, metric in (("euclidean", coords, api.METRIC_EUCLIDEAN), ("haversine", ll, api.METRIC_HAVERSINE)):
         for _ in range(2):
             st = api.travel_into_batch(bp, c, [300.0, 500.0], metric)
         torch.cuda.synchronize()
-        ms = []
-        for _ in range(5):
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record()
-            api.travel_into_batch(bp, c, [300.0, 500.0], metric)
-            b.record()
-            b.synchronize()
-            ms.append(a.elapsed_time(b))
-        t = statistics.median(ms)
+        t = device_ms(lambda: api.travel_into_batch(bp, c, [300.0, 500.0], metric))
+        st = api.travel_into_batch(bp, c, [300.0, 500.0], metric)
         res[name] = {"ms": t, "GB_per_s": nbytes / t / 1e6, "pairs_per_s": pairs / t * 1e3,
                      "status": int(st.item())}
         if hbm:
@@ -486,7 +500,7 @@ def run_sweeps(args, dev):
     out = {"workload": (f"{B:,} paper-fleet instances ({len(distinct):,} distinct x {args.sweep_copies}), "
                         "M ~ U[12, 33], 12 vehicles (4 planes), HARD 600 min cap, arrive-by windows, "
                         "Algorithm 1 with repair, at most 100 sweeps, tenure 7"),
-           "gpu_launches": 1}
+           "gpu_launches": 1, "timing": TIMING_BACK_TO_BACK}
     out["travel_matrix"] = run_travel_matrix(args, bp, insts, dev)
     for name, alg in (("algorithm_2", api.SWEEP_NEIGHBOURHOOD), ("algorithm_3", api.SWEEP_TABU)):
         params = api.sweep_params(100, api.HARD, 1000, 7, repair=True)
@@ -494,18 +508,9 @@ def run_sweeps(args, dev):
         for _ in range(max(1, args.warmup // 2)):
             api.sweep_batch(bp, alg, params, out=res)
         torch.cuda.synchronize()
-        ms = []
-        for _ in range(5):
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record()
-            api.sweep_batch(bp, alg, params, out=res)
-            b.record()
-            b.synchronize()
-            ms.append(a.elapsed_time(b))
+        t = device_ms(lambda: api.sweep_batch(bp, alg, params, out=res))
         info = res.info.view(-1, api.INFO_LEN).cpu().numpy()
         ok = info[:, api.INFO_STATUS] == 0
-        t = statistics.median(ms)
         out[name] = {"ms": t, "solves_per_s": B / t * 1e3,
                      "mission_steps_per_s": float(info[ok, api.INFO_STEPS].sum()) / t * 1e3,
                      "feasible_start_frac": float(ok.mean()),
@@ -593,15 +598,7 @@ def run_multi_start(args, distinct, default_res, dev):
     params = api.sweep_params(100, api.HARD, 1000, 7, repair=True)
     res, _ = api.sweep_batch(bp, api.SWEEP_TABU, params, orders=ords)
     torch.cuda.synchronize()
-    ms = []
-    for _ in range(5):
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        api.sweep_batch(bp, api.SWEEP_TABU, params, out=res, orders=ords)
-        b.record()
-        b.synchronize()
-        ms.append(a.elapsed_time(b))
+    t_ms = device_ms(lambda: api.sweep_batch(bp, api.SWEEP_TABU, params, out=res, orders=ords))
     info = res.info.view(len(base), R, api.INFO_LEN).cpu().numpy()
     ok = info[:, :, api.INFO_STATUS] == 0
     z = np.where(ok, info[:, :, api.INFO_Z_BEST], np.iinfo(np.int32).max).astype(np.int64)
@@ -612,7 +609,7 @@ def run_multi_start(args, distinct, default_res, dev):
     n_ok = np.maximum(ok.sum(axis=1), 1)
     mean = zz.sum(axis=1) / n_ok
     worst = np.where(ok, z, 0).max(axis=1)
-    t = statistics.median(ms)
+    t = t_ms
     return {"workload": "4,096 paper-fleet instances x 16 runs with seeded random loop orders, "
                         "Algorithm 3 (tenure 7, repair), one launch",
             "ms": t, "runs_per_s": len(insts) / t * 1e3, "instances_per_s": len(base) / t * 1e3,
@@ -622,7 +619,7 @@ def run_multi_start(args, distinct, default_res, dev):
             "best_of_16_vs_index_order_pct": float(100.0 * (1.0 - best[both].sum() / d0[both, api.INFO_Z_BEST].sum())),
             "mean_worst_minus_best_pct": float(100.0 * np.mean((worst[both] - best[both]) / best[both])),
             "mean_mean_minus_best_pct": float(100.0 * np.mean((mean[both] - best[both]) / best[both])),
-            "gpu_launches": 1}
+            "gpu_launches": 1, "timing": TIMING_BACK_TO_BACK}
 
 
 def main():
