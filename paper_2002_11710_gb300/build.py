@@ -16,6 +16,8 @@ HDR = os.path.join(ROOT, "include", "asched.h")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libasched.so")
 
+# No -use_fast_math (nor -ftz/-prec-* overrides): the travel-matrix screen's error bounds
+# rest on the documented accuracy of sinf, asinf and rsqrtf in the default mode.
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
     "-O3", "-lineinfo", "-std=c++17",
