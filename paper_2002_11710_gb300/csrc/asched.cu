@@ -59,7 +59,12 @@ constexpr int64_t kDefaultTimeoutNs = 1000000000ll;
 //   Y4[t] = {A row of prev(t), B row of t, leg prev(t) -> t, nv}   relocation, gap side
 //   S4[t] = {nv, A row of prev(t), B row of next(t), slot cost}    swap side
 //   D4[t] = {dep(prev t), arrive-by slack at t, slack at next(t), removal link ok}
-//   PRV[t] previous node; FB[v] flight of vehicle v minus the duty cap.
+//   PRV[t] previous node; FB[v] flight of vehicle v minus the duty cap;
+//   RP[t]  (after FB) a relocation's delta on t's own route when t moves to another
+//          route: removal delta plus lambda times the change of that route's overflow
+//          (penalty mode), or whether the route stays within the cap (hard mode). Kept by
+//          the batch and serving kernels, where it saves work in every relocation, and not
+//          by the single-instance kernel, whose iterations wait on the record rewrite.
 constexpr int kBufWordsPerNode = 15;
 
 // Two table layouts. Small instances keep location x mission gather tables (int32):
@@ -77,13 +82,13 @@ struct Layout {  // offsets in int32 words from the start of dynamic shared memo
 
 __host__ __device__ inline int round_up(int x, int k) { return (x + k - 1) / k * k; }
 
-__host__ __device__ inline Layout make_layout(int M, int V, int L, int nt, bool big) {
+__host__ __device__ inline Layout make_layout(int M, int V, int L, int nt, bool big, bool rp) {
   Layout y;
   y.big = big;
   y.Mp = round_up(M > 0 ? M : 1, 32);
   y.Np = round_up(M + V, 4);
   y.Vp = round_up(V, 4);
-  y.buf = kBufWordsPerNode * y.Np + y.Vp;  // R2 Y4 S4 D4 PRV, then FB
+  y.buf = kBufWordsPerNode * y.Np + y.Vp + (rp ? y.Np : 0);  // R2 Y4 S4 D4 PRV, FB, RP
   y.Ls = round_up(L, 2);
   if ((y.Ls / 2) % 2 == 0) y.Ls += 2;
   int o = 0;
@@ -294,21 +299,22 @@ struct Arr {  // an int32 array in shared memory
 };
 
 struct State {  // one buffer of per-node records (see the layout notes)
-  int base, np;
+  int base, np, vp;
   __device__ __forceinline__ int2* r2() const { return reinterpret_cast<int2*>(g_smem + base); }
   __device__ __forceinline__ int4* y4() const { return reinterpret_cast<int4*>(g_smem + base + 2 * np); }
   __device__ __forceinline__ int4* s4() const { return reinterpret_cast<int4*>(g_smem + base + 6 * np); }
   __device__ __forceinline__ int4* d4() const { return reinterpret_cast<int4*>(g_smem + base + 10 * np); }
   __device__ __forceinline__ int32_t* prv() const { return g_smem + base + 14 * np; }
   __device__ __forceinline__ int32_t* fb() const { return g_smem + base + 15 * np; }
+  __device__ __forceinline__ int32_t* rp() const { return g_smem + base + 15 * np + vp; }
   __device__ __forceinline__ int32_t& nv(int t) const { return g_smem[base + 2 * t]; }
 };
 
 struct Smem {
   Arr A, B, tabu, cmat, wm, eloc, sloc, vtype, tyl, tym, best, order, cnt, gend, gdep, gfl, glast, misc;
-  int st0, buf, np;
+  int st0, buf, np, vp;
   int warpkey_off, slots_off;
-  __device__ __forceinline__ State st(int k) const { return State{st0 + k * buf, np}; }
+  __device__ __forceinline__ State st(int k) const { return State{st0 + k * buf, np, vp}; }
   __device__ __forceinline__ uint64_t* warpkey() const {
     return reinterpret_cast<uint64_t*>(g_smem + warpkey_off);
   }
@@ -330,6 +336,7 @@ __device__ inline Smem carve(const Layout& y) {
   s.st0 = y.st0;
   s.buf = y.buf;
   s.np = y.Np;
+  s.vp = y.Vp;
   s.best = Arr{y.best};
   s.order = Arr{y.order};
   s.cnt = Arr{y.cnt};
@@ -423,7 +430,7 @@ __device__ __forceinline__ int vw_move(int from, int own) { return (from & 0x7FF
 
 // Write every record of node t into buffer S2 from its links (nx, pv), its vehicle
 // word vw and the flight f2 of that vehicle.
-template <bool PEN, bool DL, bool BIG>
+template <bool PEN, bool DL, bool BIG, bool RP>
 __device__ __forceinline__ void write_records(const Smem& sm, const Tab<BIG>& tb, const State& S2, const Ctx& c,
                                               int t, int nx, int pv, int vw, int f2) {
   const int plane = vw_plane(vw);
@@ -441,7 +448,12 @@ __device__ __forceinline__ void write_records(const Smem& sm, const Tab<BIG>& tb
     const int ct = sm.cmat[tym + t];
     const int cn = nx < c.M ? sm.cmat[tym + nx] : 0;
     const int leg = nx < c.M ? tb.a(rowA, nx) - cn : (pv < c.M ? tb.b(rowBn, pv) : 0);
-    S2.r2()[t] = make_int2(nv, leg - slot);
+    const int rem = leg - slot;
+    S2.r2()[t] = make_int2(nv, rem);
+    if (RP) {
+      const int fm = f2 - c.cap;
+      S2.rp()[t] = PEN ? rem + c.lam * (pos0(fm + rem) - pos0(fm)) : (fm + rem <= 0 ? 1 : 0);
+    }
     S2.y4()[t] = make_int4(rowA, rowB, aT - ct, nv);
     S2.s4()[t] = make_int4(nv, rowA, rowBn, slot);
     if (DL) {
@@ -463,30 +475,42 @@ __device__ __forceinline__ uint8_t move_flags(bool feas, bool tabu, bool asp, bo
 }
 
 // Relocation R(m, y): take m out, put it immediately before node y. The inputs are
-// already loaded: m's node word and removal delta, the gap record g of y, the table
-// entries a = A[row of prev(y)][m], b = B[row of y][m], y's vehicle slack fy and the
-// tabu stamp of (m, vehicle of y).
-template <bool PEN, bool DL, bool DEBUG>
+// already loaded: m's node word, removal delta and RP record, the gap record g of y, the
+// table entries a = A[row of prev(y)][m], b = B[row of y][m], y's vehicle slack fy and
+// the tabu stamp of (m, vehicle of y).
+template <bool PEN, bool DL, bool DEBUG, bool RP>
 __device__ __forceinline__ uint64_t reloc_one(const Smem& sm, const State& S, const Ctx& c, int y, int m,
-                                              int nvm, int rem, const int4& g, int a, int b, int fy,
+                                              int nvm, int rem, int rp, const int4& g, int a, int b, int fy,
                                               int stamp, int it, int Z, int zbest, const KParams& P) {
   const bool valid = (y != m) && (y != nv_next(nvm));
   const int vm = nv_veh(nvm), vy = nv_veh(g.w);
   const int ins = a + b - g.z;
   const int d = rem + ins;
-  // Same route: one flight changes by d. Different routes: the source by rem, the
-  // target by ins. Both are computed and selected, so lanes never diverge.
-  const int fm = S.fb()[vm];
+  // Same route: one flight changes by d. Different routes: the source's flight by rem
+  // (its part of the delta is m's RP record where kept), the target's by ins. Both are
+  // computed and selected, so lanes never diverge.
   const bool same = vm == vy;
   int delta;
   bool feas;
-  if (PEN) {
-    const int pen = same ? pos0(fy + d) : pos0(fm + rem) - pos0(fm) + pos0(fy + ins);
-    delta = d + c.lam * (pen - pos0(fy));
-    feas = true;
+  if (RP) {
+    const int grow = same ? d : ins;  // change of the target route's flight
+    if (PEN) {
+      delta = (same ? d : rp + ins) + c.lam * (pos0(fy + grow) - pos0(fy));
+      feas = true;
+    } else {
+      delta = d;
+      feas = (fy + grow <= 0) && (same || rp != 0);
+    }
   } else {
-    delta = d;
-    feas = same ? (fy + d <= 0) : ((fm + rem <= 0) && (fy + ins <= 0));
+    const int fm = S.fb()[vm];
+    if (PEN) {
+      const int pen = same ? pos0(fy + d) : pos0(fm + rem) - pos0(fm) + pos0(fy + ins);
+      delta = d + c.lam * (pen - pos0(fy));
+      feas = true;
+    } else {
+      delta = d;
+      feas = same ? (fy + d <= 0) : ((fm + rem <= 0) && (fy + ins <= 0));
+    }
   }
   feas = feas && !((nvm >> 24) & (g.w >> 23) & 1);  // heli-only m onto a plane
   if (DL) {
@@ -509,21 +533,23 @@ __device__ __forceinline__ uint64_t reloc_one(const Smem& sm, const State& S, co
 
 // Relocations of the mission pair (m0, m0 + 1), m0 even, before node y: every load
 // serves both (64-bit loads of consecutive table and record entries).
-template <bool PEN, bool DL, bool DEBUG, bool BIG>
+template <bool PEN, bool DL, bool DEBUG, bool BIG, bool RP>
 __device__ __forceinline__ uint64_t eval_relocate_pair(const Smem& sm, const Tab<BIG>& tb, const State& S,
                                                        const Ctx& c, int y, int m0, int it, int Z, int zbest,
                                                        const KParams& P) {
   const int4 rr = *reinterpret_cast<const int4*>(S.r2() + m0);  // {nv, rem} of m0 and m0 + 1
+  const int2 rp = RP ? *reinterpret_cast<const int2*>(S.rp() + m0) : make_int2(0, 0);
   const int4 g = S.y4()[y];  // A row, B row, leg into y, node word of y
   const int vy = nv_veh(g.w);
   const int2 a2 = tb.a2(g.x, m0);
   const int2 b2 = tb.b2(g.y, m0);
   const int2 st = tb.tabu2(vy, m0);
   const int fy = S.fb()[vy];
-  uint64_t k = reloc_one<PEN, DL, DEBUG>(sm, S, c, y, m0, rr.x, rr.y, g, a2.x, b2.x, fy, st.x, it, Z, zbest, P);
+  uint64_t k =
+      reloc_one<PEN, DL, DEBUG, RP>(sm, S, c, y, m0, rr.x, rr.y, rp.x, g, a2.x, b2.x, fy, st.x, it, Z, zbest, P);
   if (m0 + 1 < c.M)
-    k = min_u64(k, reloc_one<PEN, DL, DEBUG>(sm, S, c, y, m0 + 1, rr.z, rr.w, g, a2.y, b2.y, fy, st.y, it, Z,
-                                             zbest, P));
+    k = min_u64(k, reloc_one<PEN, DL, DEBUG, RP>(sm, S, c, y, m0 + 1, rr.z, rr.w, rp.y, g, a2.y, b2.y, fy, st.y, it,
+                                             Z, zbest, P));
   return k;
 }
 
@@ -705,7 +731,7 @@ __device__ __forceinline__ bool stage_matrix16(const KParams& P, const Layout& l
 
 // One complete search (prologue, every iteration, epilogue) of the instance in P by
 // the C CTAs of this cluster (this CTA is `rank`), with shared memory laid out by lay.
-template <bool PEN, bool DL, bool DEBUG, bool BIG>
+template <bool PEN, bool DL, bool DEBUG, bool BIG, bool RP>
 __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, const int C, const int rank) {
   const Smem sm = carve(lay);
   const Tab<BIG> tb = make_tab<BIG>(lay, P.L);
@@ -950,7 +976,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
       const int vw = nv_vw(nv);
       const int f = fl0[vw_veh(vw)];
       const int tyl = vw_plane(vw) * L;
-      write_records<PEN, DL, BIG>(sm, tb, S0, c, t, nv_next(nv), pv, vw, f);
+      write_records<PEN, DL, BIG, RP>(sm, tb, S0, c, t, nv_next(nv), pv, vw, f);
       if (t < M) {
         infeasible |= (vw >> 11) & (vw >> 10) & 1;
         if (DL) {
@@ -1018,7 +1044,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
       const int zb_eval = DEBUG ? P.dbg_zbest : zbest;
       uint64_t key = kNoKey;
       for (int y = r_y, h = r_h; y < N;) {
-        key = min_u64(key, eval_relocate_pair<PEN, DL, DEBUG, BIG>(sm, tb, S, c, y, 2 * h, it_eval, Z, zb_eval, P));
+        key = min_u64(key, eval_relocate_pair<PEN, DL, DEBUG, BIG, RP>(sm, tb, S, c, y, 2 * h, it_eval, Z, zb_eval, P));
         h += Gr;
         y += Gq;
         if (h >= H) {
@@ -1195,7 +1221,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
             }
             const int vv = vw_veh(vw);
             const int f2 = vv == va ? fa2 : (vv == vb ? fb2 : S.fb()[vv] + c.cap);
-            write_records<PEN, DL, BIG>(sm, tb, S2, c, t, nx, pv, vw, f2);
+            write_records<PEN, DL, BIG, RP>(sm, tb, S2, c, t, nx, pv, vw, f2);
             if (improved) sm.best[t] = nx;
           }
           if (tid == 0) {
@@ -1294,7 +1320,7 @@ template <bool PEN, bool DL, bool DEBUG, bool BIG>
 __global__ void __launch_bounds__(kMaxThreads, 1) tabu_kernel(const __grid_constant__ KParams P) {
   const int C = P.cluster;
   const int rank = C > 1 ? static_cast<int>(cluster_rank()) : 0;
-  solve_one<PEN, DL, DEBUG, BIG>(P, P.lay, C, rank);
+  solve_one<PEN, DL, DEBUG, BIG, false>(P, P.lay, C, rank);
 }
 
 // ------------------------------------------------------------------ batches --------
@@ -1377,12 +1403,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1) tabu_batch_kernel(const __grid
     P.info = Q.info + static_cast<int64_t>(b) * ASCHED_INFO_LEN;
     // Each instance takes the gather tables when they fit the launch's shared
     // memory, the int16 matrix otherwise.
-    const Layout small = make_layout(P.M, P.V, P.L, P.nt, false);
+    const Layout small = make_layout(P.M, P.V, P.L, P.nt, false, true);
     if (!Q.compact && small.total <= Q.smem_words) {
-      solve_one<PEN, DL, false, false>(P, small, 1, 0);
+      solve_one<PEN, DL, false, false, true>(P, small, 1, 0);
     } else {
-      const Layout big = make_layout(P.M, P.V, P.L, P.nt, true);
-      solve_one<PEN, DL, false, true>(P, big, 1, 0);
+      const Layout big = make_layout(P.M, P.V, P.L, P.nt, true, true);
+      solve_one<PEN, DL, false, true, true>(P, big, 1, 0);
     }
     __syncthreads();  // the next instance's prologue reuses shared memory
   }
@@ -1494,13 +1520,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1) serve_kernel(const __grid_cons
     const bool sizes_ok = L >= 1 && L <= Q.Lc && V >= 1 && V <= Q.Vc && M >= 0 && M <= Q.Mc &&
                           (DL == ((flags & 2) != 0));
     if (sizes_ok) {
-      const Layout small = make_layout(M, V, L, Q.nt, false);
+      const Layout small = make_layout(M, V, L, Q.nt, false, true);
       if (!Q.compact && small.total <= Q.smem_words) {
-        solve_one<PEN, DL, false, false>(P, small, C, rank);
+        solve_one<PEN, DL, false, false, true>(P, small, C, rank);
       } else {
-        const Layout big = make_layout(M, V, L, Q.nt, true);
+        const Layout big = make_layout(M, V, L, Q.nt, true, true);
         if (big.total <= Q.smem_words) {
-          solve_one<PEN, DL, false, true>(P, big, C, rank);
+          solve_one<PEN, DL, false, true, true>(P, big, C, rank);
         } else if (rank == 0 && threadIdx.x == 0) {
           P.info[ASCHED_INFO_STATUS] = ASCHED_E_TOO_LARGE;
         }
@@ -1537,14 +1563,15 @@ void* pick_kernel(bool pen, bool dl, bool debug, bool big) {
 }
 
 // Shared-memory layout for an instance: the gather tables when they fit, else the
-// int16 matrix (whose stamps limit iterations + tenure to 32,767).
-int choose_layout(int M, int V, int L, int nt, const asched_params* p, int limit_bytes, Layout* out) {
-  const Layout small = make_layout(M, V, L, nt, false);
+// int16 matrix (whose stamps limit iterations + tenure to 32,767). rp: the batch and
+// serving kernels' layout, with the RP records.
+int choose_layout(int M, int V, int L, int nt, const asched_params* p, int limit_bytes, bool rp, Layout* out) {
+  const Layout small = make_layout(M, V, L, nt, false, rp);
   if (!(p->flags & ASCHED_COMPACT_LAYOUT) && static_cast<int64_t>(small.total) * 4 + 64 <= limit_bytes) {
     *out = small;
     return ASCHED_OK;
   }
-  const Layout big = make_layout(M, V, L, nt, true);
+  const Layout big = make_layout(M, V, L, nt, true, rp);
   if (static_cast<int64_t>(big.total) * 4 + 64 > limit_bytes) return ASCHED_E_TOO_LARGE;
   if (static_cast<int64_t>(p->iterations) + p->tenure > 32767) return ASCHED_E_TOO_LARGE;
   *out = big;
@@ -1587,7 +1614,7 @@ int make_plan(const asched_instance* inst, const asched_params* p, asched_plan_t
   const int limit = max_smem_optin();
   if (limit < 0) return ASCHED_E_CUDA;
   Layout lay;
-  rc = choose_layout(M, V, inst->n_loc, inst->n_types, p, limit, &lay);
+  rc = choose_layout(M, V, inst->n_loc, inst->n_types, p, limit, false, &lay);
   if (rc != ASCHED_OK) return rc;
   const int64_t bytes = static_cast<int64_t>(lay.total) * 4;
   const int64_t items = static_cast<int64_t>(M + V) * M + static_cast<int64_t>(M) * (M - 1) / 2;
@@ -1707,7 +1734,7 @@ int launch_batch(const asched_batch* bt, const asched_params* p, const asched_ba
     int rc = check_sizes(&one, p);
     if (rc != ASCHED_OK) return rc;
     Layout lay;
-    rc = choose_layout(one.n_missions, one.n_vehicles, one.n_loc, one.n_types, p, limit, &lay);
+    rc = choose_layout(one.n_missions, one.n_vehicles, one.n_loc, one.n_types, p, limit, true, &lay);
     if (rc != ASCHED_OK) return rc;
     if (lay.total > max_words) max_words = lay.total;
   }
@@ -1819,7 +1846,7 @@ int launch_serve(const asched_server* sv, const asched_params* p, int64_t idle_n
   const int limit = max_smem_optin();
   if (limit < 0) return ASCHED_E_CUDA;
   Layout lay;  // the largest request the slots can hold sizes the launch
-  rc = choose_layout(sv->max_missions, sv->max_vehicles, sv->max_loc, sv->n_types, p, limit, &lay);
+  rc = choose_layout(sv->max_missions, sv->max_vehicles, sv->max_loc, sv->n_types, p, limit, true, &lay);
   if (rc != ASCHED_OK) return rc;
   const int64_t bytes = static_cast<int64_t>(lay.total) * 4;
   const bool pen = p->cap_mode == ASCHED_PENALTY;
