@@ -59,6 +59,47 @@ def test_batch_members_equal_single_solves_and_oracle(compact):
             np.testing.assert_array_equal(got["route_off"], r["route_off"])
 
 
+def _route_flight(inst, v, r):
+    T = inst.travel[inst.veh_type[v]]
+    e, f = inst.veh_base[v], 0
+    for m in r:
+        f += T[e][inst.pickup[m]] + T[inst.pickup[m]][inst.delivery[m]]
+        e = inst.delivery[m]
+    return f + T[e][inst.veh_base[v]] if r else 0
+
+
+@pytest.mark.parametrize("compact", [False, True], ids=["tables", "compact"])
+def test_batch_hard_cap_where_a_removal_lengthens_its_route(compact):
+    """HARD mode with caps just above the greedy schedule's longest route, on non-metric
+    matrices where taking a mission out of its route can lengthen that route past the cap:
+    such relocations are infeasible, which the batch kernel reads from its per-mission
+    source-route records. Every member equals its single solve and the oracle."""
+    insts = []
+    for seed, cap in ((500, 1790), (501, 2929), (503, 1444), (507, 1452), (510, 1958), (515, 1999)):
+        base = gen.random_instance(seed, n_loc=10, n_vehicles=3, n_missions=14, max_minutes=300,
+                                   duty_cap=100000)
+        inst = gen.Instance(**{**base.__dict__, "duty_cap": cap})
+        pb = oracle.Problem(inst, HARD, 1000)
+        status, off, route = oracle.greedy_init(pb)
+        assert status == 0
+        over = [m for v in range(inst.n_vehicles) for m in route[off[v]:off[v + 1]]
+                if _route_flight(inst, v, [x for x in route[off[v]:off[v + 1]] if x != m]) > cap]
+        assert over, seed  # the case this test is about occurs in the start schedule
+        insts.append(inst)
+    params = api.make_params(3, 60, HARD, 1000, compact=compact)
+    bp = api.BatchProblem(insts)
+    out = api.solve_batch(bp, params)
+    torch.cuda.synchronize()
+    for b, inst in enumerate(insts):
+        got = bp.unpack(out, b)
+        _same(got, _single(inst, params))
+        r = oracle.tabu_search(oracle.Problem(inst, HARD, 1000), 3, 60)
+        assert got["info"][api.INFO_STATUS] == 0
+        assert got["info"][api.INFO_Z_BEST] == r["z_best"]
+        np.testing.assert_array_equal(got["route"], r["route"])
+        np.testing.assert_array_equal(got["route_off"], r["route_off"])
+
+
 def test_batch_result_independent_of_the_mix():
     insts = _mixed_instances()
     params = api.make_params(4, 40, PENALTY, 1000)
