@@ -291,6 +291,17 @@ def test_edge_sizes(compact):
         _check_solve_vs_oracle(inst, PENALTY, 3, 25, compact=compact)
 
 
+def test_plan_launch_shapes():
+    """The default launch shape: one thread per item on one CTA for small neighbourhoods;
+    16 CTAs of about 3 sqrt(items) threads (multiples of 32 in [128, 512]) from 1,024
+    items up."""
+    cases = [(gen.tiny(0), 1, 192), (gen.paper_shaped(0), 16, 384), (gen.large(0), 16, 512)]
+    for inst, C, T in cases:
+        dp = api.DeviceProblem(inst)
+        pl = api.plan(dp, api.make_params(5, 10, PENALTY, 1000))
+        assert (pl.cluster_size, pl.block_threads) == (C, T), inst.name
+
+
 def test_large_instance_sampled_against_oracle():
     """The large configuration (400 missions, 50 vehicles, 240 locations) only fits in
     the compact layout. Its first 120 iterations: every objective is recomputed by the
