@@ -43,8 +43,8 @@ OPS_SWAP = 34
 # DRAM bytes (read + write) of one solve launch, from the ncu capture summarised in
 # profiles/tabu_kernel_paper_shaped.md. Valid only for the kernel source it was taken
 # on; any other source reports traffic as null.
-TRAFFIC_BYTES = 110848
-TRAFFIC_SOURCE_SHA = "16fc48e7bc471a84"
+TRAFFIC_BYTES = 111872
+TRAFFIC_SOURCE_SHA = "9319261f775cde53"
 
 
 def _env_int(k, d):
