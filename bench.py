@@ -43,8 +43,8 @@ OPS_SWAP = 34
 # DRAM bytes (read + write) of one solve launch, from the ncu capture summarised in
 # profiles/tabu_kernel_paper_shaped.md. Valid only for the kernel source it was taken
 # on; any other source reports traffic as null.
-TRAFFIC_BYTES = 111872
-TRAFFIC_SOURCE_SHA = "9319261f775cde53"
+TRAFFIC_BYTES = 126976
+TRAFFIC_SOURCE_SHA = "0271976a8fe2d5c8"
 
 
 def _env_int(k, d):

@@ -31,8 +31,6 @@
 //     gives the same trajectory.
 //   * The tabu list is a V x M table of iteration stamps in shared memory.
 #include <cuda_runtime.h>
-
-#include <cmath>
 #include <stdint.h>
 
 #include <mutex>
@@ -1620,31 +1618,34 @@ int make_plan(const asched_instance* inst, const asched_params* p, asched_plan_t
   if (rc != ASCHED_OK) return rc;
   const int64_t bytes = static_cast<int64_t>(lay.total) * 4;
   const int64_t items = static_cast<int64_t>(M + V) * M + static_cast<int64_t>(M) * (M - 1) / 2;
-  // Neighbourhoods of 1,024 items or more take the largest cluster and about 3 sqrt(items)
-  // threads per CTA: an iteration costs evaluation (items / threads per CTA) plus the
-  // per-warp work of reducing and applying (threads), whose sum is least near
-  // sqrt(items); measured on 1,778 to 259,800 items, 3 sqrt(items) in multiples of 32
-  // within [128, 512] was the fastest shape or within 3 % of it. Smaller neighbourhoods
-  // take one thread per item and the fewest CTAs that cover them.
+  // Neighbourhoods of 1,024 items or more take the largest cluster. The evaluation deals
+  // 32-item chunks of its item list (relocation pairs, then swaps) round-robin over the
+  // cluster's warps, so an iteration lasts as long as the warp with the most chunks, plus
+  // a little per warp (reduce, decode, rewrite, barriers): such neighbourhoods take the
+  // fewest warps per CTA, in steps of 4 (equal shares for an SM's four schedulers), that
+  // keep that largest share at its least. Measured on neighbourhoods of 1,778 to 259,800
+  // moves, this was the fastest shape or within 1 % of it. Smaller neighbourhoods take
+  // one thread per item and the fewest CTAs that cover them.
   const bool wide = items >= 1024;
+  int cl = p->cluster_size;
+  if (cl == 0 && wide) cl = kMaxCluster;
   int threads = p->block_threads;
   if (threads == 0) {
     if (wide) {
-      const int t = static_cast<int>(std::lround(3.0 * std::sqrt(static_cast<double>(items)) / 32.0)) * 32;
-      threads = t < 128 ? 128 : (t > kMaxThreads ? kMaxThreads : t);
+      const int64_t evals = static_cast<int64_t>(M + V) * ((M + 1) / 2) + static_cast<int64_t>(M) * (M - 1) / 2;
+      const int64_t chunks = (evals + 31) / 32;
+      const int64_t least = (chunks + 16 * cl - 1) / (16 * cl);  // with 16 warps per CTA
+      int w = 4;
+      while (w < 16 && (chunks + static_cast<int64_t>(w) * cl - 1) / (static_cast<int64_t>(w) * cl) > least) w += 4;
+      threads = 32 * w;
     } else {
       const int64_t want = items > M + V ? items : M + V;
       threads = want >= kMaxThreads ? kMaxThreads : (want <= 64 ? 64 : round_up(static_cast<int>(want), 32));
     }
   }
-  int cl = p->cluster_size;
   if (cl == 0) {
-    if (wide) {
-      cl = kMaxCluster;
-    } else {
-      cl = 1;
-      while (cl < kMaxCluster && items > static_cast<int64_t>(cl) * threads) cl *= 2;
-    }
+    cl = 1;
+    while (cl < kMaxCluster && items > static_cast<int64_t>(cl) * threads) cl *= 2;
   }
   plan->cluster_size = cl;
   plan->block_threads = threads;

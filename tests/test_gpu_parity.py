@@ -292,10 +292,13 @@ def test_edge_sizes(compact):
 
 
 def test_plan_launch_shapes():
-    """The default launch shape: one thread per item on one CTA for small neighbourhoods;
-    16 CTAs of about 3 sqrt(items) threads (multiples of 32 in [128, 512]) from 1,024
-    items up."""
-    cases = [(gen.tiny(0), 1, 192), (gen.paper_shaped(0), 16, 384), (gen.large(0), 16, 512)]
+    """The default launch shape: one thread per item on few CTAs for small neighbourhoods;
+    from 1,024 moves up, 16 CTAs with the fewest warps (4, 8, 12 or 16) that keep the
+    largest per-warp share of 32-item chunks at its least."""
+    two_types = gen.random_instance(8, n_loc=40, n_vehicles=25, n_missions=120, n_types=2,
+                                    duty_cap=3000, max_minutes=120)  # 495 chunks: 12 warps leave 3 to some
+    cases = [(gen.tiny(0), 1, 192), (gen.batched_member(10), 16, 128), (gen.paper_shaped(0), 16, 384),
+             (two_types, 16, 512), (gen.large(0), 16, 512)]
     for inst, C, T in cases:
         dp = api.DeviceProblem(inst)
         pl = api.plan(dp, api.make_params(5, 10, PENALTY, 1000))
