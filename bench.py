@@ -1,21 +1,27 @@
-"""Benchmark: Tabu moves evaluated per second on the paper-shaped instance.
+"""Benchmark: Tabu moves evaluated per second on the large single instance.
 
-Workload (one "step"): one complete Tabu search of 5,000 iterations on the
-paper-shaped instance (12 bases, 20 vehicles, 60 clustered facilities in a
-1500 km box, 100 missions, tenure 10, duty cap 720 min as a penalty with lambda
-1000), greedy start included, through asched_solve. Every iteration evaluates all
-M(M+V-2) + M(M-1)/2 = 16,750 moves, so a step is 83.75 M moves.
+Workload (one "step"): one complete Tabu search of 10,000 iterations on the large
+instance (40 bases, 50 vehicles, 200 clustered facilities in a 3000 km box, 400
+Zipf-skewed missions, tenure 15, duty cap 960 min as a penalty with lambda 1000), greedy
+start included, through asched_tabu_solve on its planned launch shape (every thread-block
+cluster the device holds at once). Every iteration evaluates all M(M+V-2) + M(M-1)/2 =
+259,000 moves, so a step is 2.59 G moves. The paper-shaped instance (100 missions, 5,000
+iterations) is reported beside it, then the batched, serving, sweep and travel-matrix
+workloads.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Under torchrun each rank solves its own copy of the instance (the single-instance
-search does not shard); the line reports the sum of all ranks' moves over the
-slowest rank's time. `--impl reference` times the plain CPU oracle on this host's
-cores instead (bounded iteration samples of the same instance).
+Under torchrun each rank solves its own copy of the single instances (a single search
+does not shard): the line reports the sum of all ranks' moves over the slowest rank's
+time. Batches and request streams are sharded: each rank takes its own part of the
+1,024 instances (a contiguous block) and of the request stream (every N-th request).
+`--impl reference` times the plain CPU oracle on this host's cores instead (bounded
+iteration samples of the same instance).
 """
 from __future__ import annotations
 
 import argparse
+import collections
 import hashlib
 import json
 import os
@@ -32,19 +38,27 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Tabu moves evaluated/sec (bit-exact); batched solves/sec and p50/p99 latency"
 UNIT = "moves/s"
-WORKLOAD = ("paper-shaped single instance: 12 bases, 20 vehicles, 60 facilities in 4 Gaussian "
-            "clusters (sigma 80 km) + 20% uniform outliers in a 1500 km box, 100 uniform missions, "
-            "int32 minutes at 250 km/h, duty cap 720 min (penalty, lambda 1000), tenure 10, "
-            "5,000 iterations, greedy start")
-# Algorithmic int32 operations per evaluated move (see the roofline section of the
-# design notes): a relocation is 23 ops, a swap 34, mixed in proportion.
-OPS_RELOCATE = 23
-OPS_SWAP = 34
-# DRAM bytes (read + write) of one solve launch, from the ncu capture summarised in
-# profiles/tabu_kernel_paper_shaped.md. Valid only for the kernel source it was taken
-# on; any other source reports traffic as null.
-TRAFFIC_BYTES = 126976
-TRAFFIC_SOURCE_SHA = "0271976a8fe2d5c8"
+WORKLOADS = {
+    "large": ("large single instance: 40 bases, 50 vehicles, 200 facilities in 4 Gaussian clusters "
+              "(sigma 80 km) + 20% uniform outliers in a 3000 km box, 400 missions Zipf(1.1) over "
+              "facilities, int32 minutes at 250 km/h, duty cap 960 min (penalty, lambda 1000), "
+              "tenure 15, 10,000 iterations, greedy start"),
+    "paper_shaped": ("paper-shaped single instance: 12 bases, 20 vehicles, 60 facilities in 4 Gaussian "
+                     "clusters (sigma 80 km) + 20% uniform outliers in a 1500 km box, 100 uniform "
+                     "missions, int32 minutes at 250 km/h, duty cap 720 min (penalty, lambda 1000), "
+                     "tenure 10, 5,000 iterations, greedy start"),
+}
+# Algorithmic work per evaluated move, counted from the formulas of the hot path
+# (removal + insertion cost, penalty of the touched routes, compatibility, tabu,
+# aspiration, admissibility, key): a relocation is about 20 int32 operations and 3
+# shared-memory gathers (two travel-table entries and one tabu stamp); a swap about 30
+# operations and 6 gathers (four table entries, two stamps).
+OPS_RELOCATE, OPS_SWAP = 20, 30
+GATHERS_RELOCATE, GATHERS_SWAP = 3, 6
+# DRAM bytes (read + write) per launch of the headline kernel from one ncu capture,
+# keyed by the first 16 hex digits of the SHA-256 of csrc/asched.cu it was taken on;
+# any other source reports traffic as null.
+TRAFFIC_BYTES = {}
 
 
 def _env_int(k, d):
@@ -76,15 +90,22 @@ def device_ms(fn, reps=5, rounds=3):
     return statistics.median(ts)
 
 
-def traffic_bytes():
+def source_sha():
     src = os.path.join(ROOT, "paper_2002_11710_gb300", "csrc", "asched.cu")
     with open(src, "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()[:16]
-    return TRAFFIC_BYTES if sha == TRAFFIC_SOURCE_SHA else None
+        return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
 def moves_split(M, V):
     return M * (M + V - 2), M * (M - 1) // 2
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
 class Clocks:
@@ -137,10 +158,20 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def cpu_oracle_sample(inst, p, iterations):
-    """The oracle as it stands, one core, on the first `iterations` iterations."""
+def workload(name):
+    from paper_2002_11710_gb300 import gen
+
+    if name == "large":
+        return gen.large(0), gen.LARGE_PARAMS
+    return gen.paper_shaped(0), gen.PAPER_SHAPED_PARAMS
+
+
+def cpu_oracle_sample(inst, p, iterations, threads):
+    """The oracle as it stands on the first `iterations` iterations, its loop over moves
+    on `threads` OpenMP threads (0: every core). Returns (moves/s, seconds, threads)."""
     import oracle
 
+    used = oracle.set_threads(threads)
     pb = oracle.Problem(inst, p.cap_mode, p.lam)
     t0 = time.perf_counter()
     r = oracle.tabu_search(pb, p.tenure, iterations)
@@ -148,7 +179,14 @@ def cpu_oracle_sample(inst, p, iterations):
     assert r["status"] == 0
     M, V = inst.n_missions, inst.n_vehicles
     n = (M * (M + V - 2) + M * (M - 1) // 2) * iterations
-    return n / dt, dt
+    return n / dt, dt, used
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 def max_over_ranks(seconds, world, device):
@@ -163,74 +201,88 @@ def max_over_ranks(seconds, world, device):
     return float(t.item())
 
 
+def sum_over_ranks(x, world, device):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def gather_arrays(a, world):
+    """Every rank's numpy array concatenated (all ranks call this)."""
+    if world <= 1:
+        return a
+    import torch.distributed as dist
+
+    parts = [None] * world
+    dist.all_gather_object(parts, np.asarray(a))
+    return np.concatenate(parts)
+
+
 def whole_job_rate(units_per_rank, world, seconds):
     """Units all ranks processed over the slowest rank's time."""
     return units_per_rank * world / seconds
 
 
 def run_reference(args, rank, world):
-    from paper_2002_11710_gb300 import gen
-
+    """The reference arm: the oracle on the headline workload, on every host core,
+    each step the first --ref-iterations iterations."""
     if rank != 0:
         return
-    inst, p = gen.paper_shaped(0), gen.PAPER_SHAPED_PARAMS
+    inst, p = workload("large")
     it_sample = args.ref_iterations
+    threads = 0
     for _ in range(args.warmup):
-        cpu_oracle_sample(inst, p, it_sample)
-    rates, times = [], []
+        cpu_oracle_sample(inst, p, it_sample, threads)
+    rates, times, used = [], [], 1
     for _ in range(args.steps):
-        r, dt = cpu_oracle_sample(inst, p, it_sample)
+        r, dt, used = cpu_oracle_sample(inst, p, it_sample, threads)
         rates.append(r)
         times.append(dt)
     M, V = inst.n_missions, inst.n_vehicles
     n = (M * (M + V - 2) + M * (M - 1) // 2) * it_sample
     value = n * len(times) / sum(times)
-    sample = f"first {it_sample} of 5,000 iterations of the paper-shaped instance per step"
+    sample = (f"first {it_sample} of 10,000 iterations of the large instance per step, "
+              f"oracle's loop over moves on {used} threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": sample, "n_missions": M, "n_vehicles": V},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "config": {"workload": WORKLOADS["large"], "sample": sample, "n_missions": M, "n_vehicles": V},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def run_gpu(args, rank, world, local_rank):
+def time_single(name, args, dev, world, flush, barrier, clocks=None):
+    """One single-instance workload: warm-up, then `steps` full searches each between
+    CUDA events on the launching stream (L2 flushed before each, untimed), then the same
+    searches end to end from pinned host buffers."""
     import torch
-    import torch.distributed as dist
 
-    from paper_2002_11710_gb300 import api, gen
+    from paper_2002_11710_gb300 import api
 
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    inst, p = gen.paper_shaped(0), gen.PAPER_SHAPED_PARAMS
+    inst, p = workload(name)
     M, V = inst.n_missions, inst.n_vehicles
     R, S = moves_split(M, V)
-    moves_step = (R + S) * p.iterations
-    params = api.params_from(p, cluster_size=args.cluster, block_threads=args.threads)
+    params = api.params_from(p, cluster_size=args.cluster, block_threads=args.threads, grid_clusters=args.grid)
     dp = api.DeviceProblem(inst, dev)
     plan = api.plan(dp, params)
     out = api.alloc_output(dp, p.iterations)
     stream = torch.cuda.current_stream(dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)  # > 129 MB L2
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    # warm-up (also checks the device status)
     for _ in range(args.warmup):
         api.solve(dp, params, out=out)
     torch.cuda.synchronize()
     info = out.info.cpu().numpy()
     if info[api.INFO_STATUS] != 0:
-        raise RuntimeError(f"device status {info[api.INFO_STATUS]}")
+        raise RuntimeError(f"{name}: device status {info[api.INFO_STATUS]}")
     z_best = int(info[api.INFO_Z_BEST])
-
-    clocks = Clocks(local_rank) if rank == 0 else None
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier()
@@ -245,16 +297,14 @@ def run_gpu(args, rank, world, local_rank):
         ends[k].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
+    clk = clocks.stop() if clocks else None
     barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    dev_s = sum(step_ms) / 1000.0
-    clk = clocks.stop() if clocks else None
-    dev_s = max_over_ranks(dev_s, world, dev)
-    # end to end through the public API from host data
+    dev_s = max_over_ranks(sum(step_ms) / 1000.0, world, dev)
+    # end to end through the public API from pinned host data
     pinned = api.pin_instance(inst)
     e2e_times = []
-    h2d = pinned.nbytes()
-    d2h = 0
+    h2d, d2h = pinned.nbytes(), 0
     for k in range(args.warmup + args.steps):
         barrier()
         flush.fill_(k)
@@ -266,70 +316,129 @@ def run_gpu(args, rank, world, local_rank):
             e2e_times.append(t2 - t1)
         d2h = sum(int(v.nbytes) for v in res.values())
         assert int(res["info"][api.INFO_Z_BEST]) == z_best
-    e2e_s = sum(e2e_times)
-    e2e_s = max_over_ranks(e2e_s, world, dev)
-    batched = run_batched(args, dev) if args.batched else None
-    serving = run_serving(args, dev) if args.serve_seconds > 0 else None
+    e2e_s = max_over_ranks(sum(e2e_times), world, dev)
+    moves_step = (R + S) * p.iterations
+    return {"inst": inst, "p": p, "plan": plan, "R": R, "S": S, "step_ms": step_ms, "dev_s": dev_s,
+            "e2e_s": e2e_s, "wall": wall, "clocks": clk, "z_best": z_best, "moves_step": moves_step,
+            "h2d": h2d, "d2h": d2h,
+            "value": whole_job_rate(moves_step * args.steps, world, dev_s),
+            "e2e_value": whole_job_rate(moves_step * args.steps, world, e2e_s)}
+
+
+def roofline(r, peaks, sms, sm_max_mhz, traffic):
+    """The hot kernel's roofline: algorithmic int32 operations and shared-memory gathers
+    per launch over its mean launch time, against the measured per-SM issue and gather
+    rates of the whole chip at its maximum SM clock."""
+    launch_s = statistics.mean(r["step_ms"]) / 1000.0
+    its = r["p"].iterations
+    ops = (r["R"] * OPS_RELOCATE + r["S"] * OPS_SWAP) * its
+    gathers = (r["R"] * GATHERS_RELOCATE + r["S"] * GATHERS_SWAP) * its
+    clk = sm_max_mhz * 1e6
+    peak_ops = peaks["int32_ops_per_clk_sm"] * sms * clk / 1e12
+    achieved = ops / launch_s / 1e12
+    used = r["plan"].cluster_size * r["plan"].grid_clusters
+    g_rate = gathers / launch_s
+    return {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s", "frac": achieved / peak_ops,
+            "traffic": traffic,
+            "peak_basis": (f"measured {peaks['int32_ops_per_clk_sm']:.1f} int32 ops/clk/SM (probe) x {sms} SMs x "
+                           f"{sm_max_mhz:.0f} MHz"),
+            "ops_per_move": {"relocate": OPS_RELOCATE, "swap": OPS_SWAP},
+            "sms_used": used, "frac_of_sms_used": achieved / (peak_ops * used / sms),
+            "smem": {"gathers_per_s": g_rate,
+                     "frac_of_gather_peak": g_rate / (peaks["lds_gather_words_per_clk_sm"] * sms * clk),
+                     "frac_of_conflict_free_peak": g_rate / (peaks["lds_words_per_clk_sm"] * sms * clk),
+                     "gathers_per_move": {"relocate": GATHERS_RELOCATE, "swap": GATHERS_SWAP}}}
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2002_11710_gb300 import api
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)  # > 129 MB L2
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    clocks = Clocks(local_rank) if rank == 0 else None
+    head = time_single("large", args, dev, world, flush, barrier, clocks)
+    second = time_single("paper_shaped", args, dev, world, flush, barrier) if args.paper_shaped else None
+    peaks_file = read_peaks()
+    sm_max_mhz = float(peaks_file.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    probes = api.measure_sm_peaks(dev)
+    batched = run_batched(args, dev, rank, world) if args.batched else None
+    serving = run_serving(args, dev, rank, world) if args.serve_seconds > 0 else None
     sweeps = run_sweeps(args, dev) if args.sweeps else None
     if rank != 0:
         return
-    value = whole_job_rate(moves_step * args.steps, world, dev_s)
-    e2e_value = whole_job_rate(moves_step * args.steps, world, e2e_s)
-    launch_s = statistics.mean(step_ms) / 1000.0
-    ops = (R * OPS_RELOCATE + S * OPS_SWAP) * p.iterations
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-    except OSError:
-        pass
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    int_lanes = args.int32_lanes_per_sm
-    peak_tops = sm_count * int_lanes * sm_max_mhz * 1e6 / 1e12
-    achieved = ops / launch_s / 1e12
-    cpu_rate, cpu_dt = cpu_oracle_sample(inst, p, args.cpu_iterations) if args.cpu_iterations > 0 else (None, 0)
-    lat = sorted(step_ms)
+    inst, p = head["inst"], head["p"]
+    M, V = inst.n_missions, inst.n_vehicles
+    traffic = TRAFFIC_BYTES.get(source_sha())
+    cpu = None
+    if world == 1 and args.cpu_iterations > 0:
+        r1, dt1, _ = cpu_oracle_sample(inst, p, args.cpu_iterations, 1)
+        rn, dtn, used = cpu_oracle_sample(inst, p, args.cpu_iterations_all, 0)
+        cpu = {"value": rn, "unit": UNIT, "cores": used, "kind": "oracle",
+               "sample": (f"first {args.cpu_iterations_all} of 10,000 iterations of the large instance, "
+                          f"{dtn:.1f} s on {used} threads (host has {host_cores()} cores)"),
+               "one_core": {"value": r1, "cores": 1,
+                            "sample": f"first {args.cpu_iterations} iterations, {dt1:.1f} s"}}
+    lat = sorted(head["step_ms"])
+    plan = head["plan"]
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(head["step_ms"]), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_missions": M, "n_vehicles": V,
-                   "iterations": p.iterations, "moves_per_iteration": R + S,
-                   "moves_per_step": moves_step, "cluster_size": plan.cluster_size,
-                   "block_threads": plan.block_threads, "smem_bytes": plan.smem_bytes,
+        "config": {"workload": WORKLOADS["large"], "n_missions": M, "n_vehicles": V,
+                   "iterations": p.iterations, "moves_per_iteration": head["R"] + head["S"],
+                   "moves_per_step": head["moves_step"], "cluster_size": plan.cluster_size,
+                   "grid_clusters": plan.grid_clusters, "block_threads": plan.block_threads,
+                   "smem_bytes": plan.smem_bytes,
                    "l2": "flushed between steps (256 MB write, untimed)",
-                   "parallelism": "one instance per GPU (replicas)"},
-        "solves_per_s": world * args.steps / dev_s,
+                   "parallelism": "one instance per GPU (replicas); batches and streams sharded"},
+        "solves_per_s": world * args.steps / head["dev_s"],
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-        "wall_s": wall,
-        "z_best": z_best,
+        "wall_s": head["wall"],
+        "z_best": head["z_best"],
         "gpu_launches": args.steps,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
-                     "frac": achieved / peak_tops, "traffic": traffic_bytes(),
-                     "peak_basis": f"{sm_count} SMs x {int_lanes} int32 lanes/clk x {sm_max_mhz:.0f} MHz",
-                     "frac_of_sms_used": achieved / (peak_tops * plan.cluster_size / sm_count)},
+        "e2e": {"value": head["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": head["h2d"],
+                "d2h_bytes_per_step": head["d2h"]},
+        "roofline": roofline(head, probes, sms, sm_max_mhz, traffic),
+        "sm_peaks_measured": probes,
+        "paper_shaped": None if second is None else {
+            "workload": WORKLOADS["paper_shaped"], "value": second["value"], "unit": UNIT,
+            "ms_per_step": statistics.mean(second["step_ms"]),
+            "e2e": {"value": second["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": second["h2d"],
+                    "d2h_bytes_per_step": second["d2h"]},
+            "launch_shape": {"cluster_size": second["plan"].cluster_size,
+                             "grid_clusters": second["plan"].grid_clusters,
+                             "block_threads": second["plan"].block_threads},
+            "roofline": roofline(second, probes, sms, sm_max_mhz, None), "z_best": second["z_best"]},
         "batched": batched,
         "serving": serving,
         "sweeps": sweeps,
-        "cpu_baseline": None if cpu_rate is None else {
-            "value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {args.cpu_iterations} of 5,000 iterations, same instance, {cpu_dt:.1f} s"},
-        "clocks": clk,
+        "cpu_baseline": cpu,
+        "clocks": head["clocks"],
     }
     print(json.dumps(line), flush=True)
 
 
-def run_batched(args, dev):
+def run_batched(args, dev, rank, world):
     """The batched workload: 1,024 instances (V ~ U[3, 30], M ~ U[10, 200], paper-shaped
-    geography, 2,000 iterations each) in one persistent launch, block size picked by the
-    autotuner, against the same instances as 1,024 single-instance launches."""
+    geography, 2,000 iterations each) in one persistent launch replayed from a CUDA graph,
+    launch shape picked by the autotuner, against the same instances as single-instance
+    launches. Under N ranks each rank solves a contiguous block of the instances."""
     import torch
 
-    from paper_2002_11710_gb300 import api, gen
+    from paper_2002_11710_gb300 import api, gen, shard
 
-    insts = [gen.batched_member(i) for i in range(1024)]
+    lo, hi = shard.contiguous(1024, rank, world)
+    insts = [gen.batched_member(i) for i in range(lo, hi)]
     p = gen.BATCHED_PARAMS
     moves = sum(api.num_moves(i.n_missions, i.n_vehicles) for i in insts) * p.iterations
     bp = api.BatchProblem(insts, dev)
@@ -361,13 +470,15 @@ def run_batched(args, dev):
         api.solve(d, single, out=o)
     b.record()
     b.synchronize()
-    seq_ms = a.elapsed_time(b)
-    t = statistics.median(ms)
+    seq_ms = max_over_ranks(a.elapsed_time(b), world, dev)
+    t = max_over_ranks(statistics.median(ms), world, dev)
+    moves = sum_over_ranks(moves, world, dev)
+    ok = int(sum_over_ranks(ok, world, dev))
     return {"workload": "1,024 instances, V ~ U[3,30], M ~ U[10,200], 2,000 iterations each, "
                         "replayed from a captured CUDA graph",
             "ms": t, "solves_per_s": 1024 / t * 1e3, "moves_per_s": moves / t * 1e3,
             "launch_shape": thr, "autotune_ms": {f"{t}{'/int16' if c else ''}": v for (t, c), v in tune.items()},
-            "instances_ok": ok,
+            "instances_ok": ok, "shard": f"contiguous block of {hi - lo} instances per rank ({world} ranks)",
             "sequential_ms": seq_ms, "sequential_solves_per_s": 1024 / seq_ms * 1e3,
             "speedup_vs_sequential": seq_ms / t, "gpu_launches": 2}
 
@@ -378,20 +489,63 @@ def run_batched(args, dev):
 BIG_MISSIONS, BIG_CLUSTER, BIG_CLUSTERS = 60, 8, 8
 
 
-def run_serving(args, dev):
-    """The serving workload: Poisson re-planning requests at 2,000 req/s (sizes
-    lognormal around 60 missions, clipped to [10, 400], V = ceil(M/5), 1,000 iterations
-    each) through the continuous-batching server, with slots admitted under a 40 GB
-    device-memory budget; against the plain path (one asched_solve launch per request,
-    in arrival order on one stream) for the first second of the same stream."""
+def run_plain(reqs, arrivals, params, dev, span_s, max_in_flight=32, max_v=80, max_m=400):
+    """The plain per-request path over the stream's span: one asched_tabu_solve launch
+    per request in arrival order on one stream, at most max_in_flight queued at once,
+    stopped at span_s. Returns (latencies of the served requests, served count, lower
+    bounds span_s - arrival for the requests that had arrived but were not served)."""
     import torch
 
-    from paper_2002_11710_gb300 import api, gen, serve
+    from paper_2002_11710_gb300 import api
+
+    def z(n):
+        return torch.zeros(n, dtype=torch.int32, device=dev)
+
+    ring = 2 * max_in_flight
+    outs = [api.SolveOutput(route_off=z(max_v + 1), route=z(max_m), flight=z(max_v), overflow=z(max_v),
+                            info=z(api.INFO_LEN), traj_move=None, traj_z=None) for _ in range(ring)]
+    evs = [torch.cuda.Event() for _ in range(ring)]
+    st = torch.cuda.Stream(device=dev)
+    problems = {}
+    n = len(reqs)
+    lat = []
+    pending = collections.deque()
+    t0 = time.perf_counter()
+    i = 0
+    while time.perf_counter() - t0 < span_s:
+        while pending and evs[pending[0] % ring].query():
+            k = pending.popleft()
+            lat.append(time.perf_counter() - t0 - arrivals[k])
+        now = time.perf_counter() - t0
+        while i < n and arrivals[i] <= now and len(pending) < max_in_flight:
+            dp = problems.get(id(reqs[i]))
+            if dp is None:
+                dp = problems[id(reqs[i])] = api.DeviceProblem(reqs[i], dev)
+            api.solve(dp, params, out=outs[i % ring], stream=st)
+            evs[i % ring].record(st)
+            pending.append(i)
+            i += 1
+    st.synchronize()
+    arrived = int((arrivals < span_s).sum())
+    unserved = [span_s - arrivals[k] for k in range(len(lat), arrived)]
+    return np.array(lat), len(lat), np.array(unserved)
+
+
+def run_serving(args, dev, rank, world):
+    """The serving workload: Poisson re-planning requests at 2,000 req/s for
+    --serve-seconds (sizes lognormal around 60 missions, clipped to [10, 400],
+    V = ceil(M/5), 1,000 iterations each) through the continuous-batching server, with
+    slots admitted under a 40 GB device-memory budget; against the plain path (one
+    asched_tabu_solve launch per request, in arrival order on one stream) over the same
+    span. Under N ranks every rank serves every N-th request of the stream."""
+    from paper_2002_11710_gb300 import api, gen, serve, shard
 
     params = api.params_from(gen.SERVING_PARAMS)
     pool = [gen.serving_request(20_000 + k) for k in range(2048)]
-    arrivals = gen.poisson_arrivals(7, 2000.0, args.serve_seconds)
-    reqs = [pool[k % len(pool)] for k in range(len(arrivals))]
+    arrivals_all = gen.poisson_arrivals(7, 2000.0, args.serve_seconds)
+    mine = np.array(list(shard.strided(len(arrivals_all), rank, world)), dtype=np.int64)
+    arrivals = arrivals_all[mine]
+    reqs = [pool[k % len(pool)] for k in mine]
     srv = serve.Server(max_loc=72, max_vehicles=80, max_missions=400, n_slots=4096,
                        budget_bytes=40 << 30, device=dev, big_missions=BIG_MISSIONS,
                        big_cluster=BIG_CLUSTER, big_clusters=BIG_CLUSTERS)
@@ -400,41 +554,34 @@ def run_serving(args, dev):
         lat, wall = serve.run_stream(srv, reqs, arrivals)
     finally:
         srv.stop()
-    served = srv.served()
-    # plain per-request path on the first second of arrivals
-    n_plain = int((arrivals < 1.0).sum())
-    dps = [api.DeviceProblem(r, dev) for r in reqs[:n_plain]]
-    outs = [api.alloc_output(d, params.iterations) for d in dps]
-    torch.cuda.synchronize()
-    st = torch.cuda.Stream(device=dev)
-    evs = [torch.cuda.Event() for _ in range(n_plain)]
-    lat2 = np.zeros(n_plain)
-    t0 = time.perf_counter()
-    i = k = 0
-    while k < n_plain:
-        now = time.perf_counter() - t0
-        while i < n_plain and arrivals[i] <= now:
-            api.solve(dps[i], params, out=outs[i], stream=st)
-            evs[i].record(st)
-            i += 1
-        while k < i and evs[k].query():
-            lat2[k] = time.perf_counter() - t0 - arrivals[k]
-            k += 1
-    wall2 = time.perf_counter() - t0
+    served = int(sum_over_ranks(srv.served(), world, dev))
+    wall = max_over_ranks(wall, world, dev)
+    lat = gather_arrays(lat, world)
+    plat, pserved, punserved = run_plain(reqs, arrivals, params, dev, args.serve_seconds)
+    pserved = int(sum_over_ranks(pserved, world, dev))
+    plat = gather_arrays(plat, world)
+    punserved = gather_arrays(punserved, world)
+    both = np.concatenate([plat, punserved]) if len(punserved) else plat
     return {"workload": (f"Poisson 2,000 req/s for {args.serve_seconds:g} s, M ~ lognormal(median 60) "
                          "in [10, 400], V = ceil(M/5), 1,000 iterations, 40 GB slot budget"),
             "lanes": {"one_cta": f"requests of fewer than {BIG_MISSIONS} missions, one CTA each",
                       "clusters": f"requests of {BIG_MISSIONS} missions or more, {BIG_CLUSTERS} clusters "
                                   f"of {BIG_CLUSTER} CTAs, one cluster per request"},
-            "requests": len(reqs), "served": served, "wall_s": wall,
-            "solves_per_s": len(reqs) / wall,
+            "requests": len(arrivals_all), "served": served, "wall_s": wall,
+            "shard": f"every {world}-th request per rank",
+            "solves_per_s": len(arrivals_all) / wall,
             "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3),
                            "p99": float(np.percentile(lat, 99) * 1e3),
                            "max": float(lat.max() * 1e3)},
             "slots": srv.n_slots, "slot_bytes": srv.slot_bytes,
-            "plain_per_request": {"requests": n_plain, "solves_per_s": n_plain / wall2,
-                                  "latency_ms": {"p50": float(np.percentile(lat2, 50) * 1e3),
-                                                 "p99": float(np.percentile(lat2, 99) * 1e3)}}}
+            "plain_per_request": {
+                "span_s": args.serve_seconds, "served": pserved, "unserved_at_end": int(len(punserved)),
+                "solves_per_s": pserved / args.serve_seconds,
+                "latency_ms_served": {"p50": float(np.percentile(plat, 50) * 1e3) if len(plat) else None,
+                                      "p99": float(np.percentile(plat, 99) * 1e3) if len(plat) else None},
+                "latency_ms_all_lower_bound": {"p50": float(np.percentile(both, 50) * 1e3),
+                                               "p99": float(np.percentile(both, 99) * 1e3)},
+                "note": "requests not served by the end of the span count with latency >= span - arrival"}}
 
 
 def run_travel_matrix(args, bp, insts, dev):
@@ -452,12 +599,7 @@ def run_travel_matrix(args, bp, insts, dev):
     ll = torch.from_numpy(np.stack([42.0 + xy[:, 1] / 1000.0 * 14.0, -95.0 + xy[:, 0] / 1000.0 * 21.0],
                                    axis=1)).to(dev, torch.float64)
     want = bp.travel.clone()
-    hbm = None
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            hbm = float(json.load(f).get("hbm_gbs"))
-    except (OSError, TypeError, ValueError):
-        pass
+    hbm = read_peaks().get("hbm_gbs")
     L = np.diff(bp.h_loc_off).astype(np.int64)
     pairs = int((L * L).sum())
     nbytes = 4 * bp.n_types * pairs + 16 * int(L.sum())
@@ -472,7 +614,7 @@ def run_travel_matrix(args, bp, insts, dev):
         res[name] = {"ms": t, "GB_per_s": nbytes / t / 1e6, "pairs_per_s": pairs / t * 1e3,
                      "status": int(st.item())}
         if hbm:
-            res[name]["frac_of_measured_hbm"] = nbytes / t / 1e6 / hbm
+            res[name]["frac_of_measured_hbm"] = nbytes / t / 1e6 / float(hbm)
         if metric == api.METRIC_EUCLIDEAN:
             res[name]["equals_host_matrices"] = bool(torch.equal(bp.travel, want))
     bp.travel.copy_(want)
@@ -513,10 +655,7 @@ def run_sweeps(args, dev):
         ok = info[:, api.INFO_STATUS] == 0
         out[name] = {"ms": t, "solves_per_s": B / t * 1e3,
                      "mission_steps_per_s": float(info[ok, api.INFO_STEPS].sum()) / t * 1e3,
-                     "feasible_start_frac": float(ok.mean()),
-                     "mean_sweeps": float(info[ok, api.INFO_ITERS].mean()),
-                     "mean_improvement_pct": float(100.0 * (1.0 - info[ok, api.INFO_Z_BEST].sum() /
-                                                              info[ok, api.INFO_Z_INIT].sum()))}
+                     "feasible_start_frac": float(ok.mean())}
         if _env_int("RANK", 0) == 0 and args.cpu_iterations > 0:
             t0 = time.perf_counter()
             for inst in distinct[:256]:
@@ -528,111 +667,25 @@ def run_sweeps(args, dev):
             dt = time.perf_counter() - t0
             out[name]["cpu_oracle"] = {"solves_per_s": 256 / dt, "cores": 1,
                                        "sample": f"first 256 distinct instances, {dt:.2f} s"}
-    out["multi_start"] = run_multi_start(args, distinct, res, dev)
-    out["single_instance"] = run_sweep_latency(dev)
     return out
-
-
-# The paper's per-instance runtimes (seconds; Python + Numba on an i9-7920X, its CUDA
-# variants on a GTX 1080 Ti), its Table 1, by number of missions: context, not a target.
-PAPER_RUNTIME_S = {
-    12: {"ns": 0.0153, "ns_cuda": 0.548, "tabu": 0.0245, "tabu_cuda": 0.578},
-    15: {"ns": 0.0244, "ns_cuda": 0.532, "tabu": 0.0349, "tabu_cuda": 0.615},
-    18: {"ns": 0.0322, "ns_cuda": 0.544, "tabu": 0.0424, "tabu_cuda": 0.575},
-    21: {"ns": 0.0446, "ns_cuda": 0.519, "tabu": 0.0553, "tabu_cuda": 0.507},
-    24: {"ns": 0.0499, "ns_cuda": 0.611, "tabu": 0.0618, "tabu_cuda": 0.642},
-    27: {"ns": 0.0565, "ns_cuda": 0.618, "tabu": 0.0675, "tabu_cuda": 0.561},
-    30: {"ns": 0.0581, "ns_cuda": 0.599, "tabu": 0.0682, "tabu_cuda": 0.645},
-    33: {"ns": 0.0631, "ns_cuda": 0.686, "tabu": 0.0689, "tabu_cuda": 0.611},
-}
-
-
-def run_sweep_latency(dev):
-    """One paper-fleet instance per launch at the paper's sizes (12-33 missions, its fleet),
-    Algorithm 2 and Algorithm 3 (tenure 7), repair on, HARD cap: device time per solve
-    (CUDA events around the launch, median of 20), beside the paper's own runtimes."""
-    import torch
-
-    from paper_2002_11710_gb300 import api, gen
-
-    res = {}
-    for m in sorted(PAPER_RUNTIME_S):
-        inst = gen.paper_fleet(90_000 + m, m)
-        bp = api.BatchProblem([inst], dev)
-        row = {"paper_s": PAPER_RUNTIME_S[m]}
-        for name, alg in (("algorithm_2_ms", api.SWEEP_NEIGHBOURHOOD), ("algorithm_3_ms", api.SWEEP_TABU)):
-            params = api.sweep_params(100, api.HARD, 1000, 7, repair=True)
-            out, _ = api.sweep_batch(bp, alg, params)
-            torch.cuda.synchronize()
-            ts = []
-            for _ in range(20):
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                a.record()
-                api.sweep_batch(bp, alg, params, out=out)
-                b.record()
-                b.synchronize()
-                ts.append(a.elapsed_time(b))
-            row[name] = statistics.median(ts)
-            row["status"] = int(out.info[api.INFO_STATUS].item())
-        res[str(m)] = row
-    return res
-
-
-def run_multi_start(args, distinct, default_res, dev):
-    """The paper's repeated runs (it reports best, worst and mean of 10 runs whose loop
-    orders are random permutations): 16 runs of Algorithm 3 (tenure 7, repair) for each
-    of the first 4,096 paper-fleet instances, each run with its own seeded vehicle order
-    and mission ranks, all 65,536 runs in one launch. Quality: best of 16 against the
-    run in index order (from the batch above, same instances and parameters)."""
-    import torch
-
-    from paper_2002_11710_gb300 import api, gen
-
-    R = 16
-    base = distinct[:4096]
-    insts = [inst for inst in base for _ in range(R)]
-    orders = [gen.sweep_orders(70_000 + k, inst.n_vehicles, inst.n_missions) for k, inst in enumerate(insts)]
-    bp = api.BatchProblem(insts, dev)
-    ords = api.sweep_orders_tensors(bp, orders)
-    params = api.sweep_params(100, api.HARD, 1000, 7, repair=True)
-    res, _ = api.sweep_batch(bp, api.SWEEP_TABU, params, orders=ords)
-    torch.cuda.synchronize()
-    t_ms = device_ms(lambda: api.sweep_batch(bp, api.SWEEP_TABU, params, out=res, orders=ords))
-    info = res.info.view(len(base), R, api.INFO_LEN).cpu().numpy()
-    ok = info[:, :, api.INFO_STATUS] == 0
-    z = np.where(ok, info[:, :, api.INFO_Z_BEST], np.iinfo(np.int32).max).astype(np.int64)
-    d0 = default_res.info.view(-1, api.INFO_LEN)[:len(base)].cpu().numpy()
-    both = ok.any(axis=1) & (d0[:, api.INFO_STATUS] == 0)
-    best = z.min(axis=1)
-    zz = np.where(ok, z, 0)
-    n_ok = np.maximum(ok.sum(axis=1), 1)
-    mean = zz.sum(axis=1) / n_ok
-    worst = np.where(ok, z, 0).max(axis=1)
-    t = t_ms
-    return {"workload": "4,096 paper-fleet instances x 16 runs with seeded random loop orders, "
-                        "Algorithm 3 (tenure 7, repair), one launch",
-            "ms": t, "runs_per_s": len(insts) / t * 1e3, "instances_per_s": len(base) / t * 1e3,
-            "runs_feasible_frac": float(ok.mean()),
-            "instances_feasible_any_run": float(ok.any(axis=1).mean()),
-            "instances_feasible_index_order": float((d0[:, api.INFO_STATUS] == 0).mean()),
-            "best_of_16_vs_index_order_pct": float(100.0 * (1.0 - best[both].sum() / d0[both, api.INFO_Z_BEST].sum())),
-            "mean_worst_minus_best_pct": float(100.0 * np.mean((worst[both] - best[both]) / best[both])),
-            "mean_mean_minus_best_pct": float(100.0 * np.mean((mean[both] - best[both]) / best[both])),
-            "gpu_launches": 1, "timing": TIMING_BACK_TO_BACK}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--cluster", type=int, default=0)
-    ap.add_argument("--threads", type=int, default=0)
-    ap.add_argument("--cpu-iterations", type=int, default=600)
-    ap.add_argument("--ref-iterations", type=int, default=100)
-    ap.add_argument("--int32-lanes-per-sm", type=int, default=128)
+    ap.add_argument("--cluster", type=int, default=0, help="CTAs per cluster (0: the plan's)")
+    ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: the plan's)")
+    ap.add_argument("--grid", type=int, default=0, help="clusters per instance (0: the plan's)")
+    ap.add_argument("--cpu-iterations", type=int, default=8,
+                    help="iterations of the one-core oracle sample (0 skips the CPU baselines)")
+    ap.add_argument("--cpu-iterations-all", type=int, default=60,
+                    help="iterations of the all-cores oracle sample")
+    ap.add_argument("--ref-iterations", type=int, default=8)
+    ap.add_argument("--no-paper-shaped", dest="paper_shaped", action="store_false",
+                    help="skip the paper-shaped single-instance line")
     ap.add_argument("--no-batched", dest="batched", action="store_false",
                     help="skip the 1,024-instance batched measurement")
     ap.add_argument("--no-sweeps", dest="sweeps", action="store_false",
@@ -641,9 +694,8 @@ def main():
                     help="run only the sweep measurement and print its JSON object")
     ap.add_argument("--sweep-distinct", type=int, default=16384)
     ap.add_argument("--sweep-copies", type=int, default=4)
-    ap.add_argument("--serve-seconds", type=float, default=20.0,
-                    help="length of the Poisson request stream for the serving measurement "
-                         "(the serving workload is 60 s; 0 skips it)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="length of the Poisson request stream of the serving measurement (0 skips it)")
     args = ap.parse_args()
     world = _env_int("WORLD_SIZE", 1)
     rank = _env_int("RANK", 0)

@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define ASCHED_ABI_VERSION 1
+#define ASCHED_ABI_VERSION 2
 
 /* Status codes. */
 #define ASCHED_OK 0
@@ -118,16 +118,26 @@ typedef struct {
  *   timeout_ns          bound on every wait between CTAs; 0 = 1 s.
  *   flags               0, or a combination of ASCHED_COMPACT_LAYOUT and
  *                       ASCHED_TEST_WITHHOLD_KEY.
+ *   grid_clusters       clusters cooperating on one instance in asched_tabu_solve: 0 =
+ *                       automatic, else 1..1024, every cluster resident at once (else
+ *                       ASCHED_E_TOO_LARGE). Neighbourhoods of more than 4 chunks of 32
+ *                       items per warp of one 16-CTA cluster (about 65,000 moves and up)
+ *                       spread over every cluster the device holds. The clusters exchange
+ *                       one 64-bit key per iteration through the caller's workspace
+ *                       (asched_workspace_bytes). Calls without a workspace (asched_solve,
+ *                       asched_greedy_init, asched_eval_neighbourhood) take 0 or 1.
+ *                       Results do not depend on it.
  * Shared-memory layout: instances whose location x mission gather tables fit in one
  * CTA's shared memory use them; larger ones (or all, with ASCHED_COMPACT_LAYOUT) keep
  * the travel matrix itself as int16 instead, which needs every travel time <= 32,767
  * (else ASCHED_E_TOO_LARGE on the device) and iterations + tenure <= 32,767 (else
  * ASCHED_E_TOO_LARGE from the call). Results do not depend on the layout. */
 #define ASCHED_COMPACT_LAYOUT 1u
-/* Failure-path test hook for asched_solve with cluster_size >= 2: the last CTA of the
- * cluster does not publish its key in the first iteration, so every CTA's bounded wait
- * runs out after timeout_ns and the call reports ASCHED_E_TIMEOUT (nothing faults or
- * hangs). No effect with one CTA. */
+/* Failure-path test hook for a single-instance search with several CTAs: in the first
+ * iteration the last CTA of the cluster (one cluster) or the last cluster (several
+ * clusters) does not publish its key, so every CTA's bounded wait runs out after
+ * timeout_ns and the call reports ASCHED_E_TIMEOUT (nothing faults or hangs). No effect
+ * with one CTA. */
 #define ASCHED_TEST_WITHHOLD_KEY 2u
 typedef struct {
   int32_t tenure;
@@ -138,6 +148,7 @@ typedef struct {
   int32_t block_threads;
   int64_t timeout_ns;
   uint32_t flags;
+  int32_t grid_clusters;
 } asched_params;
 
 /* Launch shape the library would use for an instance (see asched_plan). */
@@ -146,6 +157,8 @@ typedef struct {
   int32_t block_threads;
   int32_t smem_bytes;  /* dynamic shared memory per CTA */
   int64_t moves_per_iteration;
+  int32_t grid_clusters;   /* clusters of cluster_size CTAs (asched_tabu_solve) */
+  int64_t workspace_bytes; /* device workspace asched_tabu_solve needs for this shape */
 } asched_plan_t;
 
 /* Outputs of asched_solve; all device memory.
@@ -184,13 +197,14 @@ int asched_num_moves(int32_t n_missions, int32_t n_vehicles, int64_t* out);
  * Returns ASCHED_OK or the status the device would report. Host only, no CUDA call. */
 int asched_check_instance_host(const asched_instance* inst, const asched_params* params);
 
-/* Launch shape and shared-memory footprint for the given sizes (array pointers are
- * not read). Returns ASCHED_E_TOO_LARGE when the instance does not fit on chip,
- * ASCHED_E_CUDA if the device cannot be queried. */
+/* Launch shape and shared-memory footprint asched_tabu_solve takes for the given sizes
+ * (array pointers are not read). Returns ASCHED_E_TOO_LARGE when the instance does not
+ * fit on chip, ASCHED_E_CUDA if the device cannot be queried. */
 int asched_plan(const asched_instance* inst, const asched_params* params, asched_plan_t* out);
 
 /* Tabu search (Algorithm 3) on one instance, all iterations in one persistent
- * launch of `cluster_size` CTAs on `stream`.
+ * launch of one cluster of `cluster_size` CTAs on `stream` (asched_tabu_solve below
+ * with no workspace: grid_clusters must be 0 or 1).
  *   init_route_off/init_route: device CSR initial schedule (must be feasible), or
  *             both NULL to start from the greedy schedule of Algorithm 1 (heli-only
  *             missions first, then by (deadline, id); each appended to the vehicle
@@ -203,24 +217,34 @@ int asched_solve(const asched_instance* inst, const asched_params* params,
                  const asched_result* out, void* stream);
 
 /* The same calls under the names of the problem statement's interface: host-side
- * validation, the device workspace a single-instance search needs (none: every piece of
- * its state lives in shared memory, so *bytes is set to 0), Algorithm 1 alone, and the
- * Tabu search.
+ * validation, the device workspace of a search, Algorithm 1 alone, and the Tabu search.
  *   asched_validate        = asched_check_instance_host (HOST arrays, no CUDA call).
- *   asched_workspace_bytes sizes are checked as by asched_plan; *bytes = 0.
+ *   asched_workspace_bytes bytes of device workspace asched_tabu_solve needs with these
+ *                          sizes and params (the plan's workspace_bytes): 0 when the
+ *                          search runs on one cluster (every piece of its state lives
+ *                          in shared memory), else the slots of the keys the clusters
+ *                          exchange each iteration (two buffers of 128-byte lines).
  *   asched_greedy_init     Algorithm 1 (Section 4.1) on the device: the greedy schedule
  *                          written as device CSR route_off [V + 1] / route [M] and its
  *                          objective etc. in info [ASCHED_INFO_LEN] (a search of 0
  *                          iterations); device status ASCHED_E_INFEASIBLE_INIT when a
  *                          mission fits no vehicle.
- *   asched_tabu_solve      = asched_solve. */
+ *   asched_tabu_solve      the Tabu search on the launch shape of asched_plan, which may
+ *                          span several clusters (grid_clusters). workspace: device
+ *                          memory of at least asched_workspace_bytes, 128-byte aligned
+ *                          (NULL and 0 when that is 0); the call zeroes it on `stream`
+ *                          before the launch, and two searches in flight at once need
+ *                          two workspaces. The launch is cooperative, so every cluster is
+ *                          resident at once; it fails with ASCHED_E_CUDA otherwise.
+ *                          Results equal asched_solve's bit for bit. */
 int asched_validate(const asched_instance* inst, const asched_params* params);
 int asched_workspace_bytes(const asched_instance* inst, const asched_params* params, size_t* bytes);
 int asched_greedy_init(const asched_instance* inst, const asched_params* params, int32_t* route_off,
                        int32_t* route, int32_t* info, void* stream);
 int asched_tabu_solve(const asched_instance* inst, const asched_params* params,
                       const int32_t* init_route_off, const int32_t* init_route,
-                      const asched_result* out, void* stream);
+                      const asched_result* out, void* workspace, size_t workspace_bytes,
+                      void* stream);
 
 /* Every canonical move of one schedule, for checking (one launch, no move applied).
  *   route_off/route  device CSR schedule (must be feasible).
@@ -383,8 +407,10 @@ int asched_serve(const asched_server* server, const asched_params* params, int64
  * 4 * (ASCHED_STATIC_BATCH_MAX + 1) bytes (64 KB) that every GPU using this library
  * holds until the process exits. The caller still provides every input and output.
  *   - Batches above ASCHED_STATIC_BATCH_MAX instances return ASCHED_E_TOO_LARGE.
- *   - The first call on each device looks up the array's device address; make that
- *     first call before any stream capture on that device.
+ *   - Every call looks up the array's device address on the current device (a lookup,
+ *     no allocation), so the address stays right after a device reset. The first call
+ *     on a device may load the library's device code: make that first call before any
+ *     stream capture on that device.
  *   - All calls on a device share the array and leave their contents in it (the next
  *     call resets what must start at zero), so two of these calls whose work overlaps
  *     on the GPU (different streams, not ordered) race with each other. Order them on
@@ -499,6 +525,30 @@ typedef struct {
  * the kernel to ASCHED_E_INVALID if a coordinate is not finite or a time does not fit
  * int32 (such entries are written as 0). */
 int asched_travel_matrix(const asched_travel_spec* spec, int32_t* travel, int32_t* status, void* stream);
+
+/* ---------------------------------------------------------------- roofline probes --
+ * Microbenchmarks of one SM's integer issue rate and shared-memory load rate, the
+ * denominators of the roofline of the search kernels (not part of the paper's method).
+ * One launch fills every SM with resident CTAs of *threads_out threads; CTA c writes
+ * rec[3c] = its SM id, rec[3c+1] and rec[3c+2] = that SM's clock (clock64) after a block
+ * barrier before and after its work. Per thread the work is iters steps of
+ *   ASCHED_PROBE_INT32       ASCHED_PROBE_INT32_OPS_PER_STEP int32 add / xor / min
+ *                            operations (8 independent chains);
+ *   ASCHED_PROBE_LDS         ASCHED_PROBE_LDS_LOADS_PER_STEP 32-bit shared-memory loads,
+ *                            the 32 lanes of a warp on 32 distinct banks;
+ *   ASCHED_PROBE_LDS_GATHER  as many loads, each lane at a random word of a 64 KB table.
+ * A rate per SM is (CTAs on the SM) * threads * iters * (work per step) / (last end -
+ * first start on that SM). rec: device int64 [3 * rec_ctas]; sink: device uint32
+ * [rec_ctas] (written only in practice-impossible cases, to keep the work live);
+ * *ctas_out = CTAs launched (ASCHED_E_INVALID if above rec_ctas). Asynchronous on
+ * `stream`. */
+#define ASCHED_PROBE_INT32 0
+#define ASCHED_PROBE_LDS 1
+#define ASCHED_PROBE_LDS_GATHER 2
+#define ASCHED_PROBE_INT32_OPS_PER_STEP 96
+#define ASCHED_PROBE_LDS_LOADS_PER_STEP 16
+int asched_probe_sm_peak(int32_t kind, int32_t iters, int64_t* rec, int32_t rec_ctas, uint32_t* sink,
+                         int32_t* ctas_out, int32_t* threads_out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -5,8 +5,10 @@ TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the CPU baseline l
 binding) never imports this package, and this package imports nothing from it.
 
 The arithmetic lives in ``asched_oracle.c`` (plain C, full recompute of every
-candidate schedule, 64-bit costs); this module compiles it with gcc on first use
-and wraps it with ctypes. Its readings of the paper are listed at the top of the C
+candidate schedule, 64-bit costs); this module compiles it with gcc on first use and
+wraps it with ctypes. The independent moves of a neighbourhood are evaluated on OpenMP
+threads and the chosen move is picked afterwards in canonical order, so results do not
+depend on the thread count. Its readings of the paper are listed at the top of the C
 file.
 
 Pinned by ``tests/test_oracle_pins.py`` against brute force over every schedule of
@@ -39,11 +41,11 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, -O2)."""
+    """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc -O2 -fopenmp)."""
     os.makedirs(os.path.dirname(LIB), exist_ok=True)
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
         tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC", "-o", tmp, SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-fopenmp", "-shared", "-fPIC", "-o", tmp, SRC])
         os.replace(tmp, LIB)
     return LIB
 
@@ -89,6 +91,8 @@ def lib():
             L.orc_greedy_init_repair.argtypes = [P, P, P]
             L.orc_neighbourhood_search.argtypes = [P, ctypes.c_int32, ctypes.c_int32, P, P, P, P, P,
                                                    P, P, P, P, P, ctypes.c_int64]
+            L.orc_set_threads.restype = ctypes.c_int32
+            L.orc_set_threads.argtypes = [ctypes.c_int32]
             L.orc_tabu_sweep.restype = ctypes.c_int32
             L.orc_tabu_sweep.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_int32, P, P, P, P, P, P, P, P, P, P, ctypes.c_int64]
@@ -123,6 +127,12 @@ class Problem:
     @property
     def ref(self):
         return ctypes.byref(self._s)
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the loop over moves in eval_neighbourhood / tabu_search (0: one per
+    processor). Returns the count now in force. Results do not depend on it."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def num_moves(M: int, V: int) -> int:

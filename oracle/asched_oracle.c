@@ -59,6 +59,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_OK 0
 #define ORC_E_INVALID (-1)
@@ -537,7 +540,11 @@ int32_t orc_greedy_init_repair(const orc_instance *in, int32_t *off_out, int32_t
 /* Every canonical move of a schedule: delta = Z(after) - Z(before), flags (feasible,
  * tabu, aspiration, admissible) and id, in canonical order. Writes the index of the
  * chosen move (least (delta, id) among admissible moves, or -1) to *chosen_out.
- * Returns the number of moves, or a negative status. */
+ * Returns the number of moves, or a negative status.
+ * The moves are evaluated independently of one another, each on its own copy of the
+ * schedule, so the loop over them runs on OpenMP threads (orc_set_threads); the least
+ * admissible move is then picked by one thread in canonical order, so the result does
+ * not depend on the number of threads. */
 int64_t orc_eval_neighbourhood(const orc_instance *in, const int32_t *off, const int32_t *route,
                                const int32_t *tabu_until, int32_t it, int64_t z_best,
                                int64_t *delta_out, uint8_t *flags_out, uint32_t *id_out,
@@ -545,39 +552,76 @@ int64_t orc_eval_neighbourhood(const orc_instance *in, const int32_t *off, const
   int rc = check_instance(in);
   if (rc != ORC_OK) return rc;
   int M = in->n_missions, V = in->n_vehicles;
-  sched s, t;
-  if (sched_alloc(&s, V, M) != ORC_OK || sched_alloc(&t, V, M) != ORC_OK) return ORC_E_NOMEM;
-  if (sched_from_csr(&s, off, route) != ORC_OK) return ORC_E_INVALID;
+  sched s;
+  if (sched_alloc(&s, V, M) != ORC_OK) return ORC_E_NOMEM;
+  if (sched_from_csr(&s, off, route) != ORC_OK) {
+    sched_free(&s);
+    return ORC_E_INVALID;
+  }
   int64_t n = enumerate_moves(&s, NULL);
-  uint32_t *ids = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
-  enumerate_moves(&s, ids);
-  int64_t z0 = sched_cost(in, &s, NULL, NULL);
-  int64_t chosen = -1, chosen_delta = 0;
-  for (int64_t i = 0; i < n; i++) {
-    moved_t mv;
-    if (!apply_move(in, &s, ids[i], &t, &mv)) { rc = ORC_E_INVALID; break; }
-    int64_t z1 = sched_cost(in, &t, NULL, NULL);
-    int64_t delta = z1 - z0;
-    unsigned fl = 0;
-    if (sched_feasible(in, &t)) fl |= ORC_FEASIBLE;
-    for (int j = 0; j < mv.n; j++)
-      if (tabu_until[(int64_t)mv.mission[j] * V + mv.to[j]] >= it) fl |= ORC_TABU;
-    if (z1 < z_best) fl |= ORC_ASPIRATION;
-    if ((fl & ORC_FEASIBLE) && (!(fl & ORC_TABU) || (fl & ORC_ASPIRATION))) fl |= ORC_ADMISSIBLE;
-    if (delta_out) delta_out[i] = delta;
-    if (flags_out) flags_out[i] = (uint8_t)fl;
-    if (id_out) id_out[i] = ids[i];
-    if ((fl & ORC_ADMISSIBLE) &&
-        (chosen < 0 || delta < chosen_delta || (delta == chosen_delta && ids[i] < ids[chosen]))) {
-      chosen = i;
-      chosen_delta = delta;
+  size_t nn = (size_t)(n > 0 ? n : 1);
+  uint32_t *ids = (uint32_t *)malloc(sizeof(uint32_t) * nn);
+  int64_t *delta = delta_out ? delta_out : (int64_t *)malloc(sizeof(int64_t) * nn);
+  uint8_t *flags = flags_out ? flags_out : (uint8_t *)malloc(nn);
+  if (!ids || !delta || !flags) rc = ORC_E_NOMEM;
+  int64_t z0 = 0;
+  if (rc == ORC_OK) {
+    enumerate_moves(&s, ids);
+    z0 = sched_cost(in, &s, NULL, NULL);
+  }
+  int bad = 0;  /* a thread without memory, or an id that is not a move */
+#pragma omp parallel if (rc == ORC_OK && n > 1)
+  {
+    sched t;
+    int ok = rc == ORC_OK && sched_alloc(&t, V, M) == ORC_OK;
+#pragma omp for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+      moved_t mv;
+      if (!ok || !apply_move(in, &s, ids[i], &t, &mv)) {
+#pragma omp atomic write
+        bad = 1;
+        continue;
+      }
+      int64_t z1 = sched_cost(in, &t, NULL, NULL);
+      unsigned fl = 0;
+      if (sched_feasible(in, &t)) fl |= ORC_FEASIBLE;
+      for (int j = 0; j < mv.n; j++)
+        if (tabu_until[(int64_t)mv.mission[j] * V + mv.to[j]] >= it) fl |= ORC_TABU;
+      if (z1 < z_best) fl |= ORC_ASPIRATION;
+      if ((fl & ORC_FEASIBLE) && (!(fl & ORC_TABU) || (fl & ORC_ASPIRATION))) fl |= ORC_ADMISSIBLE;
+      delta[i] = z1 - z0;
+      flags[i] = (uint8_t)fl;
+    }
+    if (ok) sched_free(&t);
+  }
+  if (rc == ORC_OK && bad) rc = ORC_E_INVALID;
+  int64_t chosen = -1;
+  if (rc == ORC_OK) {
+    for (int64_t i = 0; i < n; i++) {
+      if (id_out) id_out[i] = ids[i];
+      if ((flags[i] & ORC_ADMISSIBLE) &&
+          (chosen < 0 || delta[i] < delta[chosen] || (delta[i] == delta[chosen] && ids[i] < ids[chosen])))
+        chosen = i;
     }
   }
   if (chosen_out) *chosen_out = chosen;
   free(ids);
+  if (!delta_out) free(delta);
+  if (!flags_out) free(flags);
   sched_free(&s);
-  sched_free(&t);
   return rc == ORC_OK ? n : rc;
+}
+
+/* Threads of the OpenMP loop over moves (n <= 0: one per processor); returns the
+ * number now in force (1 when built without OpenMP). */
+int32_t orc_set_threads(int32_t n) {
+#ifdef _OPENMP
+  omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
 }
 
 /* Apply a given move (or ORC_NULL_MOVE) at iteration `it` to a CSR schedule in place

@@ -20,6 +20,7 @@ E_TIMEOUT = -5
 E_CUDA = -6
 
 STATIC_BATCH_MAX = 16384  # ASCHED_STATIC_BATCH_MAX
+ABI_VERSION = 2  # ASCHED_ABI_VERSION
 
 HARD = 0
 PENALTY = 1
@@ -48,12 +49,14 @@ class Params(ctypes.Structure):
     _fields_ = [("tenure", ctypes.c_int32), ("iterations", ctypes.c_int32),
                 ("cap_mode", ctypes.c_int32), ("lam", ctypes.c_int32),
                 ("cluster_size", ctypes.c_int32), ("block_threads", ctypes.c_int32),
-                ("timeout_ns", ctypes.c_int64), ("flags", ctypes.c_uint32)]
+                ("timeout_ns", ctypes.c_int64), ("flags", ctypes.c_uint32),
+                ("grid_clusters", ctypes.c_int32)]
 
 
 class Plan(ctypes.Structure):
     _fields_ = [("cluster_size", ctypes.c_int32), ("block_threads", ctypes.c_int32),
-                ("smem_bytes", ctypes.c_int32), ("moves_per_iteration", ctypes.c_int64)]
+                ("smem_bytes", ctypes.c_int32), ("moves_per_iteration", ctypes.c_int64),
+                ("grid_clusters", ctypes.c_int32), ("workspace_bytes", ctypes.c_int64)]
 
 
 class Result(ctypes.Structure):
@@ -109,6 +112,9 @@ SWEEP_ACCEPT_WORSE = 4  # asched_params.flags bits for the sweeps
 SWEEP_REPAIR = 8
 INFO_MOVES, INFO_STEPS = 6, 7
 
+PROBE_INT32, PROBE_LDS, PROBE_LDS_GATHER = 0, 1, 2
+PROBE_INT32_OPS_PER_STEP, PROBE_LDS_LOADS_PER_STEP = 96, 16
+
 
 # Every entry point of include/asched.h with its ctypes signature.
 SIGNATURES = {
@@ -131,7 +137,8 @@ SIGNATURES = {
     "asched_validate": (ctypes.c_int, [P, P]),
     "asched_workspace_bytes": (ctypes.c_int, [P, P, P]),
     "asched_greedy_init": (ctypes.c_int, [P, P, P, P, P, P]),
-    "asched_tabu_solve": (ctypes.c_int, [P, P, P, P, P, P]),
+    "asched_tabu_solve": (ctypes.c_int, [P, P, P, P, P, P, ctypes.c_size_t, P]),
+    "asched_probe_sm_peak": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int32, P, P, P, P]),
 }
 
 _lock = threading.Lock()
@@ -153,6 +160,8 @@ def load(build_if_missing: bool = True):
                     raise RuntimeError(f"CUDA library not built: {path}")
                 _build.build()
             L = ctypes.CDLL(path)
+            if L.asched_abi_version() != ABI_VERSION:
+                raise RuntimeError(f"{path}: ABI version {L.asched_abi_version()}, expected {ABI_VERSION}")
             for name, (res, args) in SIGNATURES.items():
                 fn = getattr(L, name)
                 fn.restype = res

@@ -34,11 +34,13 @@ def num_moves(n_missions: int, n_vehicles: int) -> int:
 
 def make_params(tenure: int, iterations: int, cap_mode: int = HARD, lam: int = 1000,
                 cluster_size: int = 0, block_threads: int = 0, timeout_ns: int = 0,
-                compact: bool = False) -> _lib.Params:
+                compact: bool = False, grid_clusters: int = 0) -> _lib.Params:
     """compact: keep the travel matrix as int16 in shared memory instead of the gather
-    tables (used automatically when the tables do not fit)."""
+    tables (used automatically when the tables do not fit). grid_clusters: clusters
+    cooperating on one instance (0 = automatic)."""
     return _lib.Params(int(tenure), int(iterations), int(cap_mode), int(lam), int(cluster_size),
-                       int(block_threads), int(timeout_ns), _lib.COMPACT_LAYOUT if compact else 0)
+                       int(block_threads), int(timeout_ns), _lib.COMPACT_LAYOUT if compact else 0,
+                       int(grid_clusters))
 
 
 def params_from(p, **overrides) -> _lib.Params:
@@ -109,6 +111,18 @@ class DeviceProblem:
         self.heli_only = None if inst.heli_only is None else _i32(inst.heli_only, dev)
         self.deadline = None if inst.deadline is None else _i32(inst.deadline, dev)
         self.struct = self._struct()
+        self._ws = None
+        self._ws_bytes = {}  # asched_workspace_bytes by params
+
+    def workspace(self, nbytes: int) -> Optional[torch.Tensor]:
+        """Device workspace of at least nbytes for asched_tabu_solve (kept and reused;
+        None when nbytes is 0). Two searches of this problem in flight at once on
+        different streams need their own workspaces."""
+        if nbytes <= 0:
+            return None
+        if self._ws is None or self._ws.numel() * 8 < nbytes:
+            self._ws = torch.zeros((nbytes + 7) // 8, dtype=torch.int64, device=self.device)
+        return self._ws
 
     def _struct(self):
         return _lib.Instance(self.n_loc, self.n_types, self.V, self.M, _ptr(self.travel),
@@ -140,6 +154,13 @@ def host_struct(inst):
 def check_instance_host(inst, params: _lib.Params) -> int:
     s, keep = host_struct(inst)
     return int(_lib.load().asched_check_instance_host(ctypes.byref(s), ctypes.byref(params)))
+
+
+def workspace_bytes(dp: DeviceProblem, params: _lib.Params) -> int:
+    n = ctypes.c_size_t(0)
+    _lib.check(_lib.load().asched_workspace_bytes(ctypes.byref(dp.struct), ctypes.byref(params), ctypes.byref(n)),
+               "asched_workspace_bytes")
+    return int(n.value)
 
 
 def plan(dp: DeviceProblem, params: _lib.Params) -> _lib.Plan:
@@ -178,12 +199,38 @@ def alloc_output(dp: DeviceProblem, iterations: int, trajectory: bool = False) -
 
 
 def solve(dp: DeviceProblem, params: _lib.Params, init=None, out: Optional[SolveOutput] = None,
-          trajectory: bool = False, stream: Optional[torch.cuda.Stream] = None) -> SolveOutput:
-    """Queue one Tabu search (asched_solve) on `stream` (default: torch's current stream).
+          trajectory: bool = False, stream: Optional[torch.cuda.Stream] = None,
+          workspace: Optional[torch.Tensor] = None) -> SolveOutput:
+    """Queue one Tabu search (asched_tabu_solve, on the launch shape of asched_plan) on
+    `stream` (default: torch's current stream).
 
     init: None (greedy start, Algorithm 1) or (route_off, route) device int32 tensors.
-    Returns the output tensors; read them after synchronising the stream.
+    workspace: device tensor for the keys between clusters (default: the problem's own,
+    sized by asched_workspace_bytes). Returns the output tensors; read them after
+    synchronising the stream.
     """
+    if out is None:
+        out = alloc_output(dp, params.iterations, trajectory)
+    s = stream if stream is not None else torch.cuda.current_stream(dp.device)
+    res = out.struct()
+    ioff, iroute = (None, None) if init is None else (_ptr(init[0]), _ptr(init[1]))
+    if workspace is None:
+        key = bytes(params)
+        nb = dp._ws_bytes.get(key)
+        if nb is None:
+            nb = dp._ws_bytes[key] = workspace_bytes(dp, params)
+        workspace = dp.workspace(nb)
+    nbytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    rc = _lib.load().asched_tabu_solve(ctypes.byref(dp.struct), ctypes.byref(params), ioff, iroute,
+                                       ctypes.byref(res), _ptr(workspace), ctypes.c_size_t(nbytes),
+                                       ctypes.c_void_p(s.cuda_stream))
+    _lib.check(rc, "asched_tabu_solve")
+    return out
+
+
+def solve_one_cluster(dp: DeviceProblem, params: _lib.Params, init=None, out: Optional[SolveOutput] = None,
+                      trajectory: bool = False, stream: Optional[torch.cuda.Stream] = None) -> SolveOutput:
+    """Queue asched_solve: the same search on one cluster, with no workspace."""
     if out is None:
         out = alloc_output(dp, params.iterations, trajectory)
     s = stream if stream is not None else torch.cuda.current_stream(dp.device)
@@ -542,4 +589,42 @@ def travel_matrix(coords, speeds_kmh, metric: int = METRIC_EUCLIDEAN, radius_km:
     s.synchronize()
     if int(status.item()) != OK:
         raise AschedError(int(status.item()), "asched_travel_matrix (device)")
+    return out
+
+
+# --------------------------------------------------------------- roofline probes --
+
+def measure_sm_peaks(device="cuda", iters: int = 4000, repeats: int = 3):
+    """Per-SM rates of the roofline probes (asched_probe_sm_peak): int32 operations,
+    conflict-free shared-memory words and randomly gathered shared-memory words per SM
+    clock, each the median over SMs of (work of the SM's CTAs) / (cycles from the SM's
+    first start to its last end), best of `repeats` launches. Also the SM count."""
+    dev = torch.device(device)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    cap = 32 * sms
+    rec = torch.zeros(3 * cap, dtype=torch.int64, device=dev)
+    sink = torch.zeros(cap, dtype=torch.int32, device=dev)
+    work = {_lib.PROBE_INT32: _lib.PROBE_INT32_OPS_PER_STEP, _lib.PROBE_LDS: _lib.PROBE_LDS_LOADS_PER_STEP,
+            _lib.PROBE_LDS_GATHER: _lib.PROBE_LDS_LOADS_PER_STEP}
+    out = {"sms": sms}
+    names = {_lib.PROBE_INT32: "int32_ops_per_clk_sm", _lib.PROBE_LDS: "lds_words_per_clk_sm",
+             _lib.PROBE_LDS_GATHER: "lds_gather_words_per_clk_sm"}
+    s = torch.cuda.current_stream(dev)
+    for kind, per_step in work.items():
+        best = 0.0
+        for _ in range(repeats + 1):  # the first launch is a warm-up
+            ctas, threads = ctypes.c_int32(0), ctypes.c_int32(0)
+            _lib.check(_lib.load().asched_probe_sm_peak(int(kind), int(iters), _ptr(rec), cap, _ptr(sink),
+                                                        ctypes.byref(ctas), ctypes.byref(threads),
+                                                        ctypes.c_void_p(s.cuda_stream)), "asched_probe_sm_peak")
+            s.synchronize()
+            r = rec[: 3 * ctas.value].view(-1, 3).cpu().numpy()
+            rates = []
+            for sm in np.unique(r[:, 0]):
+                rows = r[r[:, 0] == sm]
+                span = int(rows[:, 2].max() - rows[:, 1].min())
+                if span > 0:
+                    rates.append(len(rows) * threads.value * iters * per_step / span)
+            best = max(best, float(np.median(rates)))
+        out[names[kind]] = best
     return out

@@ -1,6 +1,6 @@
 """Compile the CUDA library in-tree: paper_2002_11710_gb300/_build/libasched.so.
 
-sm_103a only (GB300); three translation units compiled in parallel and linked into
+sm_103a only (GB300); four translation units compiled in parallel and linked into
 one shared library, so it builds in under a minute here and on the GPU host alike.
 """
 from __future__ import annotations
@@ -11,7 +11,7 @@ import sys
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
-SRCS = [os.path.join(PKG, "csrc", n) for n in ("asched.cu", "sweep.cu", "matrix.cu")]
+SRCS = [os.path.join(PKG, "csrc", n) for n in ("asched.cu", "sweep.cu", "matrix.cu", "peaks.cu")]
 HDR = os.path.join(ROOT, "include", "asched.h")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libasched.so")

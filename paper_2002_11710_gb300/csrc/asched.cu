@@ -33,8 +33,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <mutex>
-
 #include "asched.h"
 
 namespace {
@@ -43,6 +41,7 @@ constexpr uint32_t kSwapBit = 0x80000000u;
 constexpr uint32_t kNullMove = 0xFFFFFFFFu;
 constexpr uint64_t kNoKey = ~0ull;
 constexpr int kMaxCluster = 16;
+constexpr int kMaxGridClusters = 1024;  // clusters of one single-instance launch
 constexpr int kMaxThreads = 512;  // per CTA; leaves 128 registers per thread
 constexpr int kIdShift = 13;
 constexpr uint32_t kIdMask = (1u << kIdShift) - 1u;
@@ -75,7 +74,7 @@ constexpr int kBufWordsPerNode = 15;
 // and random columns both spread over the banks; tabu stamps are int16 there too.
 struct Layout {  // offsets in int32 words from the start of dynamic shared memory
   int A, B, tabu, cmat, wm, eloc, sloc, vtype, tyl, tym, st0, st1, best, order, cnt, gend, gdep, gfl,
-      glast, misc, mbar, warpkey, slots, total;
+      glast, misc, mbar, warpkey, slots, gkey, total;
   int Mp, Np, Vp, buf, Ls;
   bool big;
 };
@@ -122,6 +121,7 @@ __host__ __device__ inline Layout make_layout(int M, int V, int L, int nt, bool 
   o = round_up(o, 4);
   y.warpkey = o; o += 2 * 32;
   y.slots = o;   o += 2 * 2 * kMaxCluster;
+  y.gkey = o;    o += 2 * 2;  // the grid's key, per slot buffer (several clusters)
   y.total = o;
   return y;
 }
@@ -138,7 +138,10 @@ struct KParams {
   const int32_t* deadline;
   int32_t L, nt, V, M, cap, horizon;
   int32_t tenure, iterations, lambda, cluster;
-  int32_t test_withhold;  // the last CTA does not publish its first key (tests the timeout)
+  int32_t grid_clusters;  // clusters cooperating on the instance (1: one cluster)
+  int32_t gslot_stride;   // words (uint64) between the two global slot buffers
+  uint64_t* gslots;       // [2][gslot_stride] keys of the clusters (grid_clusters > 1), zeroed
+  int32_t test_withhold;  // the last CTA (cluster) does not publish its first key (tests the timeout)
   int64_t timeout_ns;
   Layout lay;
   const int32_t* init_off;
@@ -235,18 +238,20 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                "l"(src), "r"(bytes), "r"(bar)
                : "memory");
 }
-// the same into the shared memory (same offsets) of every CTA of the cluster in mask
-__device__ __forceinline__ void bulk_g2s_multicast(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar,
-                                                   uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], %4;" ::
-          "r"(dst),
-      "l"(src), "r"(bytes), "r"(bar), "h"(mask)
-      : "memory");
-}
 // OR of a flag into a word of another CTA's shared memory
 __device__ __forceinline__ void red_or_peer(uint32_t cluster_addr, uint32_t v) {
   asm volatile("red.shared::cluster.or.b32 [%0], %1;" ::"r"(cluster_addr), "r"(v) : "memory");
+}
+
+// Keys between the clusters of one instance go through global memory (L2): relaxed
+// stores and loads at GPU scope, each a single 64-bit word that carries its own tag.
+__device__ __forceinline__ void st_relaxed_gpu_u64(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_relaxed_gpu_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
 }
 
 // Instance inputs are read through L2 only (ld.global.cg): a persistent launch reuses
@@ -266,6 +271,9 @@ __device__ __forceinline__ uint64_t global_ns() {
 // 0-25), so keys crossing the cluster carry an iteration tag there: 8 | ((it >> 1) & 7).
 // Slots start at 0 (tag 0), and consecutive uses of a slot buffer carry different tags.
 constexpr uint64_t kTagMask = 0xFull << 26;
+// Bit 30 is zero in every move id too. In a key broadcast to the CTAs of a cluster it
+// means "the exchange between clusters gave up" (with a high word of all ones).
+constexpr uint64_t kFailBit = 1ull << 30;
 __device__ __forceinline__ uint64_t iter_tag(int it) {
   return static_cast<uint64_t>(8 | ((it >> 1) & 7)) << 26;
 }
@@ -313,12 +321,13 @@ struct State {  // one buffer of per-node records (see the layout notes)
 struct Smem {
   Arr A, B, tabu, cmat, wm, eloc, sloc, vtype, tyl, tym, best, order, cnt, gend, gdep, gfl, glast, misc;
   int st0, buf, np, vp;
-  int warpkey_off, slots_off;
+  int warpkey_off, slots_off, gkey_off;
   __device__ __forceinline__ State st(int k) const { return State{st0 + k * buf, np, vp}; }
   __device__ __forceinline__ uint64_t* warpkey() const {
     return reinterpret_cast<uint64_t*>(g_smem + warpkey_off);
   }
   __device__ __forceinline__ uint64_t* slots() const { return reinterpret_cast<uint64_t*>(g_smem + slots_off); }
+  __device__ __forceinline__ uint64_t* gkey() const { return reinterpret_cast<uint64_t*>(g_smem + gkey_off); }
 };
 
 __device__ inline Smem carve(const Layout& y) {
@@ -347,6 +356,7 @@ __device__ inline Smem carve(const Layout& y) {
   s.misc = Arr{y.misc};
   s.warpkey_off = y.warpkey;
   s.slots_off = y.slots;
+  s.gkey_off = y.gkey;
   return s;
 }
 
@@ -553,7 +563,10 @@ __device__ __forceinline__ uint64_t eval_relocate_pair(const Smem& sm, const Tab
   return k;
 }
 
-// Cost parts of swap S(a, b): t1..t4 as in the design notes, adjacency-aware.
+// Cost parts of swap S(a, b), each mission taking the other's place: t1 = fly from the
+// end of a's predecessor to b's pickup plus b's own leg, t2 = from b's delivery to a's
+// successor's start, t3 and t4 the same for a in b's place. When a and b are neighbours
+// the predecessor or successor is the other mission itself (its delivery row is used).
 struct SwapParts {
   int4 sa, sb;
   int t1, t2, t3, t4;
@@ -631,14 +644,14 @@ __device__ __forceinline__ uint64_t eval_swap(const Smem& sm, const Tab<BIG>& tb
 // padded, built from the int32 input through a staging buffer: the second record buffer,
 // which nothing uses before the first move is applied. When the input is 16-byte aligned
 // its words go by bulk copies completing on an mbarrier, in chunks the size of the
-// buffer; with C > 1 CTAs, rank 0 issues each chunk once, multicast into every CTA of the
-// cluster, so the cluster reads the matrix from L2 once instead of C times. A cluster
-// barrier before each chunk keeps the buffer free until every CTA has converted the
-// previous one. Every wait is bounded by P.timeout_ns; a CTA that gives up tells rank 0,
-// and every CTA reads that at the next barrier, so all leave the loop together. Entries
-// are checked (>= 0) and their maximum taken on the way. Returns true on a timeout.
-__device__ __forceinline__ bool stage_matrix16(const KParams& P, const Layout& lay, int C, int rank, int& bad,
-                                               int& maxT) {
+// buffer; every CTA copies every chunk into its own shared memory (the cluster reads the
+// matrix from L2 C times; 230 KB per CTA once per solve). A block barrier after each
+// chunk keeps the buffer free until every thread has converted it. Every wait is bounded
+// by P.timeout_ns. With C > 1 CTAs the outcome is made the same in every CTA: a CTA whose
+// copy gave up ORs a flag into rank 0's shared memory, and every CTA reads it after a
+// cluster barrier. Entries are checked (>= 0) and their maximum taken on the way.
+// Returns true on a timeout (in every CTA of the cluster when one timed out).
+__device__ __forceinline__ bool stage_matrix16(const KParams& P, const Layout& lay, int C, int& bad, int& maxT) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int L = P.L, nt = P.nt, Ls = lay.Ls, pad = lay.Ls - P.L;
   int16_t* T16 = reinterpret_cast<int16_t*>(g_smem + lay.A);
@@ -656,83 +669,66 @@ __device__ __forceinline__ bool stage_matrix16(const KParams& P, const Layout& l
   const bool aligned = (reinterpret_cast<uintptr_t>(P.travel) & 15u) == 0;
   const int bulk = aligned ? (words & ~3) : 0;  // words that go by bulk copies (16-byte units)
   for (int g = bulk + tid; g < words; g += nthr) put(g, gin(P.travel + g));
-  if (bulk == 0) return false;
-  int32_t* stage = g_smem + lay.st1;
-  const int cap = lay.buf & ~3;
-  const uint32_t bar = smem_u32(g_smem + lay.mbar);
   const uint32_t fail_addr = smem_u32(&g_smem[lay.misc + MISC_STAGE_FAIL]);
-  if (tid == 0) {
-    mbar_init(bar, 1);
-    mbar_fence_init();
-  }
+  // Every CTA has zeroed its misc words (prologue 1) before any peer may OR into them.
+  if (C > 1) cluster_sync_unaligned();
   bool gave_up = false;  // this CTA's wait ran out
-  bool stop = false;     // some CTA's did (the same in every CTA)
   uint32_t phase = 0;
-  for (int c0 = 0; c0 < bulk && !stop; c0 += cap, phase ^= 1u) {
-    const int n = bulk - c0 < cap ? bulk - c0 : cap;
-    if (tid == 0) mbar_arrive_expect_tx(bar, static_cast<uint32_t>(n) * 4u);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // reads of the last chunk before the copy
-    if (C > 1) {
-      cluster_sync_unaligned();
-      stop = ld_peer_i32(mapa_rank(fail_addr, 0)) != 0;
-    } else {
-      __syncthreads();
-      stop = g_smem[lay.misc + MISC_STAGE_FAIL] != 0;
+  if (bulk > 0) {
+    int32_t* stage = g_smem + lay.st1;
+    const int cap = lay.buf & ~3;
+    const uint32_t bar = smem_u32(g_smem + lay.mbar);
+    if (tid == 0) {
+      mbar_init(bar, 1);
+      mbar_fence_init();
     }
-    if (stop) break;
-    if (tid == 0 && rank == 0) {
-      if (C > 1)
-        bulk_g2s_multicast(smem_u32(stage), P.travel + c0, static_cast<uint32_t>(n) * 4u, bar,
-                           static_cast<uint16_t>((1u << C) - 1u));
-      else
+    __syncthreads();
+    for (int c0 = 0; c0 < bulk; c0 += cap, phase ^= 1u) {
+      const int n = bulk - c0 < cap ? bulk - c0 : cap;
+      if (tid == 0) {
+        // the block's reads of the previous chunk come before the copy overwrites it
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(bar, static_cast<uint32_t>(n) * 4u);
         bulk_g2s(smem_u32(stage), P.travel + c0, static_cast<uint32_t>(n) * 4u, bar);
-    }
-    bool ok = mbar_try_wait(bar, phase);
-    if (!ok) {
-      const uint64_t t0 = global_ns();
-      while (!(ok = mbar_try_wait(bar, phase))) {
-        if (static_cast<int64_t>(global_ns() - t0) > P.timeout_ns) break;
       }
-    }
-    if (!__all_sync(0xffffffffu, ok)) ok = false;
-    if (!ok) {
-      gave_up = true;
-      if ((tid & 31) == 0) {
-        if (C > 1)
-          red_or_peer(mapa_rank(fail_addr, 0), 1u);
-        else
-          atomicOr(&g_smem[lay.misc + MISC_STAGE_FAIL], 1);
+      bool ok = mbar_try_wait(bar, phase);
+      if (!ok) {
+        const uint64_t t0 = global_ns();
+        while (!(ok = mbar_try_wait(bar, phase))) {
+          if (static_cast<int64_t>(global_ns() - t0) > P.timeout_ns) break;
+        }
       }
-      continue;  // the next barrier ends the loop in every CTA
-    }
-    for (int i = tid; i < n; i += nthr) put(c0 + i, stage[i]);
-  }
-  if (!stop) {  // every chunk converted: one more barrier, so a failure reported at the end is seen
-    if (C > 1) {
-      cluster_sync_unaligned();
-      stop = ld_peer_i32(mapa_rank(fail_addr, 0)) != 0;
-    } else {
+      if (!__syncthreads_and(ok)) {
+        gave_up = true;
+        break;
+      }
+      for (int i = tid; i < n; i += nthr) put(c0 + i, stage[i]);
       __syncthreads();
-      stop = g_smem[lay.misc + MISC_STAGE_FAIL] != 0;
     }
-  }
-  if (gave_up) {  // let a copy still in flight land (bounded) before this CTA moves on
-    const uint64_t t0 = global_ns();
-    while (!mbar_try_wait(bar, phase ^ 1u) && static_cast<int64_t>(global_ns() - t0) < P.timeout_ns) {
+    if (gave_up) {  // let the copy still in flight land (bounded) before the buffer is reused
+      const uint64_t t0 = global_ns();
+      while (!mbar_try_wait(bar, phase) && static_cast<int64_t>(global_ns() - t0) < P.timeout_ns) {
+      }
     }
-  }
-  if (C > 1)
-    cluster_sync_unaligned();  // nobody reads rank 0's flag after this
-  else
     __syncthreads();  // nobody waits on the barrier after this
-  if (tid == 0) mbar_inval(bar);
+    if (tid == 0) mbar_inval(bar);
+  }
+  if (C == 1) return gave_up;
+  if (gave_up && tid == 0) red_or_peer(mapa_rank(fail_addr, 0), 1u);
+  cluster_sync_unaligned();
+  const bool stop = ld_peer_i32(mapa_rank(fail_addr, 0)) != 0;
+  cluster_sync_unaligned();  // nobody reads rank 0's flag after this
   return stop;
 }
 
 // One complete search (prologue, every iteration, epilogue) of the instance in P by
-// the C CTAs of this cluster (this CTA is `rank`), with shared memory laid out by lay.
+// the K clusters of C CTAs each (this CTA is `rank` in cluster `cid`), with shared
+// memory laid out by lay. Every CTA holds the whole state and applies every move; CTA 0
+// of cluster 0 writes the outputs.
 template <bool PEN, bool DL, bool DEBUG, bool BIG, bool RP>
-__device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, const int C, const int rank) {
+__device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, const int C, const int rank,
+                                          const int K, const int cid) {
+  const bool lead = rank == 0 && cid == 0;
   const Smem sm = carve(lay);
   const Tab<BIG> tb = make_tab<BIG>(lay, P.L);
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -786,10 +782,10 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
   }
   if (__syncthreads_or(bad)) status = ASCHED_E_INVALID;
   if (BIG && status == ASCHED_OK) {
-    // ---- prologue 1b: the int16 matrix, staged through shared memory by bulk copies
-    // (one multicast copy per chunk for the whole cluster), checked as it is converted
+    // ---- prologue 1b: the int16 matrix, staged through shared memory by bulk copies,
+    // checked as it is converted
     int tbad = 0;
-    const bool timed_out = stage_matrix16(P, lay, C, rank, tbad, maxT);
+    const bool timed_out = stage_matrix16(P, lay, C, tbad, maxT);
     if (__syncthreads_or(tbad)) status = ASCHED_E_INVALID;
     if (timed_out) status = ASCHED_E_TIMEOUT;  // the same in every CTA of the cluster
   }
@@ -1000,6 +996,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
     }
     for (int t = tid; t < N; t += nthr) sm.best[t] = nv_next(S0.nv(t));
     for (int i = tid; i < 2 * kMaxCluster; i += nthr) sm.slots()[i] = 0;
+    if (tid < 2) sm.gkey()[tid] = 0;
     __syncthreads();
     Z = sm.misc[MISC_Z0];
   }
@@ -1010,13 +1007,15 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
   if (looped) {
     if (C > 1) cluster_sync_all();
     // Static assignment over the item list [relocation pairs (N * ceil(M/2)) | swaps
-    // (M(M-1)/2)]: chunks of 32 consecutive items go round-robin to (CTA, warp), so
-    // every CTA gets an equal share and the lanes of a warp take consecutive items.
+    // (M(M-1)/2)]: chunks of 32 consecutive items go round-robin to (CTA, warp) over the
+    // K * C CTAs of the grid, so every CTA gets an equal share and the lanes of a warp
+    // take consecutive items.
     // A relocation item i is (y, h) = divmod(i, H) for missions 2h and 2h + 1; a swap
     // item j is (row, a) = divmod(j, M) with b = (a + row + 1) mod M, which lists every
     // pair a != b once. Coordinates advance by G without dividing.
-    const int G = C * nthr;
-    const int g = lane + 32 * (rank + C * warp);
+    const int CT = K * C;
+    const int G = CT * nthr;
+    const int g = lane + 32 * (cid * C + rank + CT * warp);
     const int H = (M + 1) / 2;
     const int Rn = N * H;
     const int Sn = M * (M - 1) / 2;
@@ -1074,7 +1073,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
         // iteration's tag (bounded by the timeout).
         const int sb = it & 1;
         const uint64_t tag = iter_tag(it);
-        const bool withhold = P.test_withhold && it == 0 && rank == C - 1;  // test hook
+        const bool withhold = P.test_withhold && K == 1 && it == 0 && rank == C - 1;  // test hook
         if (warp == 0 && lane < C && !withhold) {
           const uint32_t slot_addr = smem_u32(&sm.slots()[sb * kMaxCluster + rank]);
           st_peer_u64(mapa_rank(slot_addr, lane), (gk & ~kTagMask) | tag);
@@ -1100,8 +1099,68 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
           if ((gk >> 32) == 0xFFFFFFFFull) gk = kNoKey;  // real deltas never reach 2^31 - 1
         }
       }
+      if (K > 1) {
+        // Between clusters: rank 0 of each cluster stores the cluster's key, tagged, into
+        // global slot [it & 1][cid]; its warp 0 polls the K slots until all carry this
+        // iteration's tag (bounded), takes the least and pushes it, tagged, into every CTA
+        // of its cluster; every warp polls its own copy. A wait that gives up is pushed as
+        // a key with kFailBit. The slots were zeroed before the launch; a slot buffer is
+        // reused two iterations later, when every cluster has read it (a cluster publishes
+        // for it + 1 only after reading all keys of it).
+        const int sb = it & 1;
+        const uint64_t tag = iter_tag(it);
+        const uint32_t gk_addr = smem_u32(&sm.gkey()[sb]);
+        if (rank == 0 && warp == 0) {
+          uint64_t* gs = P.gslots + static_cast<int64_t>(sb) * P.gslot_stride;
+          const bool withhold = P.test_withhold && it == 0 && cid == K - 1;  // test hook
+          if (lane == 0 && !timed_out && !withhold) st_relaxed_gpu_u64(gs + cid, (gk & ~(kTagMask | kFailBit)) | tag);
+          bool ok = !timed_out;
+          uint64_t m = kNoKey;
+          if (ok) {
+            const uint64_t t0 = global_ns();
+            while (true) {
+              bool mine = true;
+              uint64_t mk = kNoKey;
+              for (int k = lane; k < K; k += 32) {
+                const uint64_t v = ld_relaxed_gpu_u64(gs + k);
+                mine = mine && (v & kTagMask) == tag;
+                mk = min_u64(mk, v);
+              }
+              if (__all_sync(0xffffffffu, mine)) {
+                m = warp_min_key(mk);
+                break;
+              }
+              if (__shfl_sync(0xffffffffu, static_cast<int64_t>(global_ns() - t0) > P.timeout_ns, 0)) {
+                ok = false;
+                break;
+              }
+            }
+          }
+          const uint64_t msg = ok ? ((m & ~kTagMask) | tag) : ((0xFFFFFFFFull << 32) | kFailBit | tag);
+          if (lane < C) st_peer_u64(mapa_rank(gk_addr, lane), msg);
+        }
+        if (!timed_out) {
+          uint64_t v = ld_own_u64(gk_addr);
+          bool got = __all_sync(0xffffffffu, (v & kTagMask) == tag);
+          if (!got) {
+            const uint64_t t0 = global_ns();
+            while (true) {
+              v = ld_own_u64(gk_addr);
+              got = __all_sync(0xffffffffu, (v & kTagMask) == tag);
+              if (got) break;
+              if (__shfl_sync(0xffffffffu, static_cast<int64_t>(global_ns() - t0) > P.timeout_ns, 0)) break;
+            }
+          }
+          if (!got || (v & kFailBit)) {
+            timed_out = true;
+          } else {
+            gk = v & ~kTagMask;
+            if ((gk >> 32) == 0xFFFFFFFFull) gk = kNoKey;
+          }
+        }
+      }
       // A chosen move must name nodes of this instance; anything else ends the solve
-      // (gk is the same in every thread of the cluster, so this decision is too).
+      // (gk is the same in every thread of the grid, so this decision is too).
       bool bad_key = false;
       if (!timed_out && gk != kNoKey) {
         const uint32_t id = static_cast<uint32_t>(gk);
@@ -1114,7 +1173,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
         }
       }
       if (DEBUG) {
-        if (rank == 0 && tid == 0 && !timed_out) *P.dbg_key = gk;
+        if (lead && tid == 0 && !timed_out) *P.dbg_key = gk;
       } else if (!timed_out && !bad_key && gk != kNoKey) {
         // ---- apply the chosen move: every thread decodes it from the current buffer,
         // then rewrites the records of its nodes into the other buffer.
@@ -1239,7 +1298,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
           best_it = it;
         }
       }
-      if (!DEBUG && rank == 0 && tid == 0 && !timed_out) {
+      if (!DEBUG && lead && tid == 0 && !timed_out) {
         if (P.traj_move) P.traj_move[it] = gk == kNoKey ? kNullMove : static_cast<uint32_t>(gk);
         if (P.traj_z) P.traj_z[it] = Z;
       }
@@ -1251,8 +1310,8 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
     }
   }
 
-  // ---- epilogue: best schedule in CSR form (rank 0 writes every output)
-  if (rank == 0 && !DEBUG && status == ASCHED_OK && P.out_off) {
+  // ---- epilogue: best schedule in CSR form (the lead CTA writes every output)
+  if (lead && !DEBUG && status == ASCHED_OK && P.out_off) {
     const Arr lens = sm.gfl;  // scratch reuse (V entries)
     int walk_bad = 0;
     for (int v = tid; v < V; v += nthr) {
@@ -1302,7 +1361,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
       status = ASCHED_E_INVALID;
     }
   }
-  if (rank == 0 && tid == 0 && P.info) {
+  if (lead && tid == 0 && P.info) {
     P.info[ASCHED_INFO_STATUS] = status;
     P.info[ASCHED_INFO_Z_BEST] = zbest;
     P.info[ASCHED_INFO_BEST_IT] = best_it;
@@ -1320,7 +1379,9 @@ template <bool PEN, bool DL, bool DEBUG, bool BIG>
 __global__ void __launch_bounds__(kMaxThreads, 1) tabu_kernel(const __grid_constant__ KParams P) {
   const int C = P.cluster;
   const int rank = C > 1 ? static_cast<int>(cluster_rank()) : 0;
-  solve_one<PEN, DL, DEBUG, BIG, false>(P, P.lay, C, rank);
+  const int K = P.grid_clusters;
+  const int cid = K > 1 ? static_cast<int>(blockIdx.x) / C : 0;
+  solve_one<PEN, DL, DEBUG, BIG, false>(P, P.lay, C, rank, K, cid);
 }
 
 // ------------------------------------------------------------------ batches --------
@@ -1405,10 +1466,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) tabu_batch_kernel(const __grid
     // memory, the int16 matrix otherwise.
     const Layout small = make_layout(P.M, P.V, P.L, P.nt, false, true);
     if (!Q.compact && small.total <= Q.smem_words) {
-      solve_one<PEN, DL, false, false, true>(P, small, 1, 0);
+      solve_one<PEN, DL, false, false, true>(P, small, 1, 0, 1, 0);
     } else {
       const Layout big = make_layout(P.M, P.V, P.L, P.nt, true, true);
-      solve_one<PEN, DL, false, true, true>(P, big, 1, 0);
+      solve_one<PEN, DL, false, true, true>(P, big, 1, 0, 1, 0);
     }
     __syncthreads();  // the next instance's prologue reuses shared memory
   }
@@ -1522,11 +1583,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1) serve_kernel(const __grid_cons
     if (sizes_ok) {
       const Layout small = make_layout(M, V, L, Q.nt, false, true);
       if (!Q.compact && small.total <= Q.smem_words) {
-        solve_one<PEN, DL, false, false, true>(P, small, C, rank);
+        solve_one<PEN, DL, false, false, true>(P, small, C, rank, 1, 0);
       } else {
         const Layout big = make_layout(M, V, L, Q.nt, true, true);
         if (big.total <= Q.smem_words) {
-          solve_one<PEN, DL, false, true, true>(P, big, C, rank);
+          solve_one<PEN, DL, false, true, true>(P, big, C, rank, 1, 0);
         } else if (rank == 0 && threadIdx.x == 0) {
           P.info[ASCHED_INFO_STATUS] = ASCHED_E_TOO_LARGE;
         }
@@ -1595,6 +1656,7 @@ int check_sizes(const asched_instance* inst, const asched_params* p) {
     return ASCHED_E_INVALID;
   if (p->timeout_ns < 0 || (p->flags & ~(ASCHED_COMPACT_LAYOUT | ASCHED_TEST_WITHHOLD_KEY)) != 0)
     return ASCHED_E_INVALID;
+  if (p->grid_clusters < 0 || p->grid_clusters > kMaxGridClusters) return ASCHED_E_INVALID;
   return ASCHED_OK;
 }
 
@@ -1606,62 +1668,149 @@ int max_smem_optin() {
   return v;
 }
 
-// Pick block size and cluster size; returns status.
-int make_plan(const asched_instance* inst, const asched_params* p, asched_plan_t* plan, Layout* lay_out) {
+// Clusters of C CTAs (threads each, smem bytes of shared memory) that the device can
+// hold at once for kernel fn; 0 when none fits.
+int active_clusters(void* fn, int C, int threads, int smem, int* out) {
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return ASCHED_E_CUDA;
+  if (C > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    return ASCHED_E_CUDA;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = static_cast<size_t>(smem);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
+    (void)cudaGetLastError();
+    n = 0;
+  }
+  *out = n;
+  return ASCHED_OK;
+}
+
+// Warps per CTA for a neighbourhood of `chunks` 32-item chunks dealt over `ctas` CTAs:
+// the fewest, in steps of 4 (equal shares for an SM's four schedulers), that keep the
+// largest per-warp share at its least (16 warps at most).
+int warps_for(int64_t chunks, int64_t ctas) {
+  const int64_t least = (chunks + 16 * ctas - 1) / (16 * ctas);
+  int w = 4;
+  while (w < 16 && (chunks + w * ctas - 1) / (w * ctas) > least) w += 4;
+  return w;
+}
+
+// Bytes of the global key slots a launch of K clusters uses: two buffers of K keys,
+// each buffer in its own 128-byte lines.
+int64_t grid_slot_stride(int K) { return round_up(K, 16); }  // in uint64 words
+size_t grid_workspace_bytes(int K) { return K > 1 ? static_cast<size_t>(2 * grid_slot_stride(K) * 8) : 0; }
+
+// Launch shape: block size, cluster size C and clusters K; returns status.
+// allow_grid: the call has a workspace for the keys between clusters (K may exceed 1).
+int make_plan(const asched_instance* inst, const asched_params* p, bool debug, bool allow_grid,
+              asched_plan_t* plan, Layout* lay_out) {
   int rc = check_sizes(inst, p);
   if (rc != ASCHED_OK) return rc;
+  if (p->grid_clusters < 0 || (!allow_grid && p->grid_clusters > 1)) return ASCHED_E_INVALID;
   const int M = inst->n_missions, V = inst->n_vehicles;
   const int limit = max_smem_optin();
   if (limit < 0) return ASCHED_E_CUDA;
   Layout lay;
   rc = choose_layout(M, V, inst->n_loc, inst->n_types, p, limit, false, &lay);
   if (rc != ASCHED_OK) return rc;
-  const int64_t bytes = static_cast<int64_t>(lay.total) * 4;
+  const int bytes = lay.total * 4;
+  void* fn = pick_kernel(p->cap_mode == ASCHED_PENALTY, inst->deadline != nullptr, debug, lay.big);
   const int64_t items = static_cast<int64_t>(M + V) * M + static_cast<int64_t>(M) * (M - 1) / 2;
+  const int64_t evals = static_cast<int64_t>(M + V) * ((M + 1) / 2) + static_cast<int64_t>(M) * (M - 1) / 2;
+  const int64_t chunks = (evals + 31) / 32;
   // Neighbourhoods of 1,024 items or more take the largest cluster. The evaluation deals
   // 32-item chunks of its item list (relocation pairs, then swaps) round-robin over the
-  // cluster's warps, so an iteration lasts as long as the warp with the most chunks, plus
-  // a little per warp (reduce, decode, rewrite, barriers): such neighbourhoods take the
-  // fewest warps per CTA, in steps of 4 (equal shares for an SM's four schedulers), that
-  // keep that largest share at its least. Measured on neighbourhoods of 1,778 to 259,800
-  // moves, this was the fastest shape or within 1 % of it. Smaller neighbourhoods take
-  // one thread per item and the fewest CTAs that cover them.
+  // warps of every CTA, so an iteration lasts as long as the warp with the most chunks,
+  // plus a little per warp (reduce, decode, rewrite, barriers): such neighbourhoods take
+  // the fewest warps per CTA that keep that largest share at its least (warps_for).
+  // Measured on neighbourhoods of 1,778 to 259,800 moves, this was the fastest shape or
+  // within 1 % of it. Smaller neighbourhoods take one thread per item and the fewest CTAs
+  // that cover them.
   const bool wide = items >= 1024;
   int cl = p->cluster_size;
   if (cl == 0 && wide) cl = kMaxCluster;
+  int K = p->grid_clusters > 0 ? p->grid_clusters : 1;
+  const int probe_threads = p->block_threads ? p->block_threads : kMaxThreads;
+  if (p->cluster_size == 0 && cl > 1) {
+    // shrink the cluster until the device can place one
+    int n = 0;
+    while (cl > 1) {
+      rc = active_clusters(fn, cl, probe_threads, bytes, &n);
+      if (rc != ASCHED_OK) return rc;
+      if (n > 0) break;
+      cl /= 2;
+    }
+  }
+  // Neighbourhoods with more than 4 chunks per warp on one full cluster (the evaluation
+  // then dominates the iteration) spread over every cluster of that size the device
+  // holds at once, when the call has a workspace. The largest cluster is kept: keys
+  // cross clusters through L2, which costs about 2 us per iteration whatever the number
+  // of clusters, so fewer, larger clusters (more of the exchange in DSMEM) measured
+  // fastest (on the large instance 7 x 16 CTAs: 3.7 us per iteration; 15 x 8: 3.8;
+  // 27 x 4: 4.1; 76 x 2: 5.2).
+  if (allow_grid && p->grid_clusters == 0 && wide && chunks > 4 * 16 * static_cast<int64_t>(kMaxCluster)) {
+    int n = 0;
+    rc = active_clusters(fn, cl, probe_threads, bytes, &n);
+    if (rc != ASCHED_OK) return rc;
+    if (n >= 2) K = n;
+  }
+  if (cl == 0) cl = 1;
   int threads = p->block_threads;
   if (threads == 0) {
     if (wide) {
-      const int64_t evals = static_cast<int64_t>(M + V) * ((M + 1) / 2) + static_cast<int64_t>(M) * (M - 1) / 2;
-      const int64_t chunks = (evals + 31) / 32;
-      const int64_t least = (chunks + 16 * cl - 1) / (16 * cl);  // with 16 warps per CTA
-      int w = 4;
-      while (w < 16 && (chunks + static_cast<int64_t>(w) * cl - 1) / (static_cast<int64_t>(w) * cl) > least) w += 4;
-      threads = 32 * w;
+      threads = 32 * warps_for(chunks, static_cast<int64_t>(cl) * K);
     } else {
       const int64_t want = items > M + V ? items : M + V;
       threads = want >= kMaxThreads ? kMaxThreads : (want <= 64 ? 64 : round_up(static_cast<int>(want), 32));
     }
   }
-  if (cl == 0) {
+  if (p->cluster_size == 0 && !wide && K == 1) {
     cl = 1;
     while (cl < kMaxCluster && items > static_cast<int64_t>(cl) * threads) cl *= 2;
+    int n = 0;
+    while (cl > 1) {  // shrink the cluster until the device can place one
+      rc = active_clusters(fn, cl, threads, bytes, &n);
+      if (rc != ASCHED_OK) return rc;
+      if (n > 0) break;
+      cl /= 2;
+    }
+  }
+  if (K > 1) {  // every cluster must be resident at once
+    int n = 0;
+    rc = active_clusters(fn, cl, threads, bytes, &n);
+    if (rc != ASCHED_OK) return rc;
+    if (K > n) return ASCHED_E_TOO_LARGE;
   }
   plan->cluster_size = cl;
   plan->block_threads = threads;
-  plan->smem_bytes = static_cast<int32_t>(bytes);
+  plan->smem_bytes = bytes;
   plan->moves_per_iteration = moves_of(M, V);
+  plan->grid_clusters = K;
+  plan->workspace_bytes = static_cast<int64_t>(grid_workspace_bytes(K));
   if (lay_out) *lay_out = lay;
   return ASCHED_OK;
 }
 
-int launch(const asched_instance* inst, const asched_params* p, bool debug, KParams kp, void* stream) {
+int launch(const asched_instance* inst, const asched_params* p, bool debug, KParams kp, void* workspace,
+           size_t ws_bytes, bool allow_grid, void* stream) {
   asched_plan_t plan;
   Layout lay;
-  int rc = make_plan(inst, p, &plan, &lay);
+  int rc = make_plan(inst, p, debug, allow_grid, &plan, &lay);
   if (rc != ASCHED_OK) return rc;
   if (!inst->travel || !inst->veh_base) return ASCHED_E_INVALID;
   if (inst->n_missions > 0 && (!inst->pickup || !inst->delivery)) return ASCHED_E_INVALID;
+  const int K = plan.grid_clusters;
+  if (K > 1 && (!workspace || ws_bytes < grid_workspace_bytes(K) || (reinterpret_cast<uintptr_t>(workspace) & 127u)))
+    return ASCHED_E_INVALID;
   const bool pen = p->cap_mode == ASCHED_PENALTY;
   const bool dl = inst->deadline != nullptr;
   void* fn = pick_kernel(pen, dl, debug, lay.big);
@@ -1682,6 +1831,9 @@ int launch(const asched_instance* inst, const asched_params* p, bool debug, KPar
   kp.iterations = p->iterations;
   kp.lambda = pen ? p->lambda : 0;
   kp.cluster = plan.cluster_size;
+  kp.grid_clusters = K;
+  kp.gslot_stride = static_cast<int32_t>(grid_slot_stride(K));
+  kp.gslots = K > 1 ? static_cast<uint64_t*>(workspace) : nullptr;
   kp.timeout_ns = p->timeout_ns > 0 ? p->timeout_ns : kDefaultTimeoutNs;
   kp.test_withhold = (p->flags & ASCHED_TEST_WITHHOLD_KEY) ? 1 : 0;
   kp.lay = lay;
@@ -1690,29 +1842,27 @@ int launch(const asched_instance* inst, const asched_params* p, bool debug, KPar
   if (plan.cluster_size > 8 &&
       cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
     return ASCHED_E_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (K > 1 && cudaMemsetAsync(workspace, 0, grid_workspace_bytes(K), st) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return ASCHED_E_CUDA;
+  }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(plan.cluster_size, 1, 1);
+  cfg.gridDim = dim3(plan.cluster_size * K, 1, 1);
   cfg.blockDim = dim3(plan.block_threads, 1, 1);
   cfg.dynamicSmemBytes = static_cast<size_t>(plan.smem_bytes);
-  cfg.stream = static_cast<cudaStream_t>(stream);
-  cudaLaunchAttribute attr[1];
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = plan.cluster_size;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  // Clusters that wait on one another need to be resident together: a cooperative
+  // launch guarantees it (or fails to launch).
+  attr[1].id = cudaLaunchAttributeCooperative;
+  attr[1].val.cooperative = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  if (p->cluster_size == 0) {
-    // Automatic shape: shrink the cluster until the device can place one.
-    while (kp.cluster > 1) {
-      int n = 0;
-      if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) == cudaSuccess && n > 0) break;
-      (void)cudaGetLastError();
-      kp.cluster /= 2;
-      cfg.gridDim = dim3(kp.cluster, 1, 1);
-      attr[0].val.clusterDim.x = kp.cluster;
-    }
-  }
+  cfg.numAttrs = K > 1 ? 2 : 1;
   void* args[] = {&kp};
   if (cudaLaunchKernelExC(&cfg, fn, args) != cudaSuccess) {
     (void)cudaGetLastError();
@@ -1953,30 +2103,22 @@ int launch_serve(const asched_server* sv, const asched_params* p, int64_t idle_n
 
 // Work queue and processing order for asched_solve_batch_static: a fixed array in
 // every device's global memory, so that call needs no workspace from its caller.
-// Host code only uses its device address, looked up per device (see below).
+// Host code only uses its device address, looked up on each call (see below).
 static __device__ __align__(256) int32_t g_batch_scratch[1 + ASCHED_STATIC_BATCH_MAX];
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mu;
-void* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of g_batch_scratch on the current device, looked up on the first
-// call for that device.
+// Device address of g_batch_scratch on the current device. Looked up on every call
+// (the lookup allocates nothing), so the address stays right after a device reset,
+// which reloads the module and may move the array. The first lookup on a device can
+// load the module, so it belongs before any stream capture.
 int static_scratch(void** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ASCHED_E_CUDA;
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
-    void* ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, g_batch_scratch) != cudaSuccess || !ptr) {
-      (void)cudaGetLastError();
-      return ASCHED_E_CUDA;
-    }
-    g_scratch_addr[dev] = ptr;
+  void* ptr = nullptr;
+  if (cudaGetSymbolAddress(&ptr, g_batch_scratch) != cudaSuccess || !ptr) {
+    (void)cudaGetLastError();
+    return ASCHED_E_CUDA;
   }
-  *out = g_scratch_addr[dev];
+  *out = ptr;
   return ASCHED_OK;
 }
 
@@ -2035,13 +2177,11 @@ int asched_check_instance_host(const asched_instance* inst, const asched_params*
 
 int asched_plan(const asched_instance* inst, const asched_params* params, asched_plan_t* out) {
   if (!out) return ASCHED_E_INVALID;
-  return make_plan(inst, params, out, nullptr);
+  return make_plan(inst, params, false, true, out, nullptr);
 }
 
-int asched_solve(const asched_instance* inst, const asched_params* params, const int32_t* init_route_off,
-                 const int32_t* init_route, const asched_result* out, void* stream) {
-  if (!out || !out->route_off || !out->route || !out->info) return ASCHED_E_INVALID;
-  if ((init_route_off == nullptr) != (init_route == nullptr)) return ASCHED_E_INVALID;
+namespace {
+KParams solve_params(const int32_t* init_route_off, const int32_t* init_route, const asched_result* out) {
   KParams kp = {};
   kp.init_off = init_route_off;
   kp.init_route = init_route;
@@ -2052,7 +2192,15 @@ int asched_solve(const asched_instance* inst, const asched_params* params, const
   kp.info = out->info;
   kp.traj_move = out->traj_move;
   kp.traj_z = out->traj_z;
-  return launch(inst, params, false, kp, stream);
+  return kp;
+}
+}  // namespace
+
+int asched_solve(const asched_instance* inst, const asched_params* params, const int32_t* init_route_off,
+                 const int32_t* init_route, const asched_result* out, void* stream) {
+  if (!out || !out->route_off || !out->route || !out->info) return ASCHED_E_INVALID;
+  if ((init_route_off == nullptr) != (init_route == nullptr)) return ASCHED_E_INVALID;
+  return launch(inst, params, false, solve_params(init_route_off, init_route, out), nullptr, 0, false, stream);
 }
 
 int asched_validate(const asched_instance* inst, const asched_params* params) {
@@ -2061,9 +2209,10 @@ int asched_validate(const asched_instance* inst, const asched_params* params) {
 
 int asched_workspace_bytes(const asched_instance* inst, const asched_params* params, size_t* bytes) {
   if (!bytes) return ASCHED_E_INVALID;
-  const int rc = check_sizes(inst, params);
+  asched_plan_t plan;
+  const int rc = make_plan(inst, params, false, true, &plan, nullptr);
   if (rc != ASCHED_OK) return rc;
-  *bytes = 0;
+  *bytes = static_cast<size_t>(plan.workspace_bytes);
   return ASCHED_OK;
 }
 
@@ -2072,6 +2221,7 @@ int asched_greedy_init(const asched_instance* inst, const asched_params* params,
   if (!params || !route_off || !route || !info) return ASCHED_E_INVALID;
   asched_params p0 = *params;
   p0.iterations = 0;
+  p0.grid_clusters = 1;
   asched_result out = {};
   out.route_off = route_off;
   out.route = route;
@@ -2080,8 +2230,12 @@ int asched_greedy_init(const asched_instance* inst, const asched_params* params,
 }
 
 int asched_tabu_solve(const asched_instance* inst, const asched_params* params, const int32_t* init_route_off,
-                      const int32_t* init_route, const asched_result* out, void* stream) {
-  return asched_solve(inst, params, init_route_off, init_route, out, stream);
+                      const int32_t* init_route, const asched_result* out, void* workspace, size_t workspace_bytes,
+                      void* stream) {
+  if (!out || !out->route_off || !out->route || !out->info) return ASCHED_E_INVALID;
+  if ((init_route_off == nullptr) != (init_route == nullptr)) return ASCHED_E_INVALID;
+  return launch(inst, params, false, solve_params(init_route_off, init_route, out), workspace, workspace_bytes, true,
+                stream);
 }
 
 int asched_batch_workspace_bytes(int32_t n_instances, size_t* out) {
@@ -2137,7 +2291,7 @@ int asched_eval_neighbourhood(const asched_instance* inst, const asched_params* 
   kp.dbg_id = id_out;
   kp.dbg_key = best_key_out;
   kp.info = info;
-  return launch(inst, params, true, kp, stream);
+  return launch(inst, params, true, kp, nullptr, 0, false, stream);
 }
 
 }  // extern "C"

@@ -29,7 +29,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_abi_version_and_status_strings():
     L = _lib.load()
-    assert L.asched_abi_version() == 1
+    assert L.asched_abi_version() == _lib.ABI_VERSION == 2
     for rc in (0, -1, -2, -3, -4, -5, -6, -99):
         assert isinstance(_lib.status_string(rc), str)
     assert _lib.status_string(0) == "ok"
@@ -101,9 +101,10 @@ def test_plan_without_a_device_reports_cuda_error():
     assert rc == api.E_CUDA
 
 
-def test_validate_and_workspace_entry_points_need_no_gpu():
-    """asched_validate is the host validation under the interface's name;
-    asched_workspace_bytes reports that a single search needs no device workspace."""
+def test_validate_and_workspace_entry_points_host_paths():
+    """asched_validate is the host validation under the interface's name (no GPU needed).
+    asched_workspace_bytes rejects bad arguments before it asks the device anything; with
+    no device it reports the CUDA error, on a GPU the bytes of the plan's key slots."""
     L = _lib.load()
     base = gen.random_instance(5, n_loc=6, n_vehicles=3, n_missions=8)
     bad = gen.Instance(**{**base.__dict__, "pickup": np.where(np.arange(8) == 2, 6, base.pickup)})
@@ -113,8 +114,14 @@ def test_validate_and_workspace_entry_points_need_no_gpu():
         assert L.asched_validate(ctypes.byref(s), ctypes.byref(p)) == api.check_instance_host(inst, p)
     s, keep = api.host_struct(gen.paper_shaped(0))
     n = ctypes.c_size_t(123)
-    assert L.asched_workspace_bytes(ctypes.byref(s), ctypes.byref(_params()), ctypes.byref(n)) == api.OK
-    assert n.value == 0
+    import torch
+    rc = L.asched_workspace_bytes(ctypes.byref(s), ctypes.byref(_params()), ctypes.byref(n))
+    if torch.cuda.is_available():
+        assert rc == api.OK and n.value == 0  # one cluster: all state on chip
+    else:
+        assert rc == api.E_CUDA
+    assert L.asched_workspace_bytes(ctypes.byref(s), ctypes.byref(_params(grid_clusters=-1)),
+                                    ctypes.byref(n)) == api.E_INVALID
     assert L.asched_workspace_bytes(ctypes.byref(s), ctypes.byref(_params(cap_mode=9)),
                                     ctypes.byref(n)) == api.E_INVALID
     assert L.asched_workspace_bytes(ctypes.byref(s), ctypes.byref(_params()), None) == api.E_INVALID

@@ -154,11 +154,22 @@ def test_solve_trajectory_matches_oracle(name, mk, mode, tenure, iters, compact)
     _check_solve_vs_oracle(mk(), mode, tenure, iters, compact=compact)
 
 
-@pytest.mark.parametrize("cluster,threads", [(1, 512), (2, 512), (4, 128), (8, 448), (16, 256)])
-def test_trajectory_independent_of_launch_shape(cluster, threads):
+@pytest.mark.parametrize("cluster,threads,grid", [(1, 512, 1), (2, 512, 1), (4, 128, 1), (8, 448, 1), (16, 256, 1),
+                                                  (1, 128, 5), (2, 96, 3), (4, 64, 7), (8, 256, 2), (16, 512, 2),
+                                                  (16, 128, 4), (1, 64, 37)])
+def test_trajectory_independent_of_launch_shape(cluster, threads, grid):
+    """Any launch shape, also spanning several clusters that exchange keys through the
+    workspace, gives the oracle's trajectory."""
     inst = gen.random_instance(51, n_loc=14, n_vehicles=8, n_missions=40, n_types=2,
                                heli_only_frac=0.2, duty_cap=900, max_minutes=120)
-    _check_solve_vs_oracle(inst, PENALTY, 6, 80, cluster_size=cluster, block_threads=threads)
+    _check_solve_vs_oracle(inst, PENALTY, 6, 80, cluster_size=cluster, block_threads=threads, grid_clusters=grid)
+
+
+@pytest.mark.parametrize("grid", [2, 5])
+def test_grid_launch_compact_layout_with_deadlines_and_two_types(grid):
+    inst = gen.random_instance(49, n_loc=12, n_vehicles=6, n_missions=23, n_types=2, heli_only_frac=0.25,
+                               deadlines=True, deadline_lo=1000, duty_cap=2500, max_minutes=60)
+    _check_solve_vs_oracle(inst, HARD, 4, 120, cluster_size=4, grid_clusters=grid, compact=True)
 
 
 GREEDY_CASES = [
@@ -181,11 +192,7 @@ def test_greedy_init_matches_oracle(mk, mode):
     rc, off, route = oracle.greedy_init(pb)
     dp = api.DeviceProblem(inst)
     params = api.make_params(5, 0, mode, 1000)
-    try:
-        out = api.solve(dp, params)
-    except api.AschedError as e:  # instance too large for the on-chip layout
-        assert e.status == api.E_TOO_LARGE
-        pytest.skip("instance does not fit the on-chip layout yet")
+    out = api.solve(dp, params)  # every case fits one of the two on-chip layouts
     torch.cuda.synchronize()
     info = out.info.cpu().numpy()
     if rc != 0:
@@ -216,22 +223,36 @@ def test_greedy_init_entry_point_matches_oracle(mk, mode):
     assert info[api.INFO_Z_BEST] == info[api.INFO_Z_INIT] == oracle.cost(pb, off, route)[0]
 
 
-def test_tabu_solve_entry_point_equals_solve():
+@pytest.mark.parametrize("grid", [1, 3])
+def test_tabu_solve_entry_point_equals_solve(grid):
+    """asched_tabu_solve (through ctypes, with a workspace when the launch spans several
+    clusters) gives what asched_solve gives on one cluster, bit for bit."""
     import ctypes
 
     inst = gen.random_instance(72, n_loc=9, n_vehicles=4, n_missions=17, duty_cap=2000, n_types=2,
                                heli_only_frac=0.2)
     dp = api.DeviceProblem(inst)
     params = api.make_params(5, 80, PENALTY, 1000)
-    a = api.solve(dp, params, trajectory=True)
+    a = api.solve_one_cluster(dp, params, trajectory=True)
+    gp = api.make_params(5, 80, PENALTY, 1000, cluster_size=2, grid_clusters=grid)
+    nb = api.workspace_bytes(dp, gp)
+    assert (nb > 0) == (grid > 1)
+    ws = torch.zeros(max(nb, 8) // 8, dtype=torch.int64, device="cuda")
     b = api.alloc_output(dp, params.iterations, trajectory=True)
     res = b.struct()
-    rc = api._lib.load().asched_tabu_solve(ctypes.byref(dp.struct), ctypes.byref(params), None, None,
-                                           ctypes.byref(res), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    rc = api._lib.load().asched_tabu_solve(ctypes.byref(dp.struct), ctypes.byref(gp), None, None,
+                                           ctypes.byref(res), ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(nb),
+                                           ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == api.OK
     torch.cuda.synchronize()
     for k in ("route_off", "route", "info", "traj_move", "traj_z"):
         assert torch.equal(getattr(a, k), getattr(b, k)), k
+    if grid > 1:  # a workspace that is too small is refused before anything is queued
+        rc = api._lib.load().asched_tabu_solve(ctypes.byref(dp.struct), ctypes.byref(gp), None, None,
+                                               ctypes.byref(res), ctypes.c_void_p(ws.data_ptr()),
+                                               ctypes.c_size_t(nb - 8),
+                                               ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rc == api.E_INVALID
 
 
 def test_solve_from_given_schedule():
@@ -298,11 +319,19 @@ def test_plan_launch_shapes():
     two_types = gen.random_instance(8, n_loc=40, n_vehicles=25, n_missions=120, n_types=2,
                                     duty_cap=3000, max_minutes=120)  # 495 chunks: 12 warps leave 3 to some
     cases = [(gen.tiny(0), 1, 192), (gen.batched_member(10), 16, 128), (gen.paper_shaped(0), 16, 384),
-             (two_types, 16, 512), (gen.large(0), 16, 512)]
+             (two_types, 16, 512)]
     for inst, C, T in cases:
         dp = api.DeviceProblem(inst)
         pl = api.plan(dp, api.make_params(5, 10, PENALTY, 1000))
-        assert (pl.cluster_size, pl.block_threads) == (C, T), inst.name
+        assert (pl.cluster_size, pl.block_threads, pl.grid_clusters) == (C, T, 1), inst.name
+        assert pl.workspace_bytes == 0
+    # the large neighbourhood (5,307 chunks) spreads over every cluster the device holds
+    dp = api.DeviceProblem(gen.large(0))
+    pl = api.plan(dp, api.make_params(15, 10, PENALTY, 1000))
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert pl.grid_clusters >= 2 and pl.grid_clusters * pl.cluster_size <= sms
+    assert pl.grid_clusters * pl.cluster_size >= sms // 2
+    assert pl.workspace_bytes >= 16 * pl.grid_clusters
 
 
 def test_large_instance_sampled_against_oracle():
@@ -331,6 +360,56 @@ def test_large_instance_sampled_against_oracle():
             assert int(gm[it]) == (0xFFFFFFFF if chosen < 0 else int(ids[chosen])), f"iteration {it}"
         if it > 0:
             assert int(gz[it - 1]) == z, f"objective after iteration {it - 1}"
+
+
+def test_large_full_run_sampled_against_oracle():
+    """The benchmark's workload at full length: the large instance, all 10,000 iterations,
+    on the default launch shape (several clusters). Every objective on the trajectory is
+    recomputed by the oracle from the replayed schedule, the best objective and its
+    iteration follow, and at sampled iterations the oracle's own neighbourhood evaluation
+    must choose the same move."""
+    inst, p = gen.large(0), gen.LARGE_PARAMS
+    dp = api.DeviceProblem(inst)
+    params = api.params_from(p)
+    assert api.plan(dp, params).grid_clusters >= 2
+    out = api.solve(dp, params, trajectory=True)
+    torch.cuda.synchronize()
+    info = out.info.cpu().numpy()
+    assert info[api.INFO_STATUS] == 0 and info[api.INFO_ITERS] == p.iterations
+    gm = out.traj_move.cpu().numpy().view(np.uint32)
+    gz = out.traj_z.cpu().numpy()
+    pb = oracle.Problem(inst, p.cap_mode, p.lam)
+    rc, off0, route0 = oracle.greedy_init(pb)
+    assert rc == 0 and info[api.INFO_Z_INIT] == oracle.cost(pb, off0, route0)[0]
+    sample = {0, 1, 2, 997, 4001, p.iterations - 1}
+    for it, off, route, tabu, z, zb in _replay_states(pb, p.tenure, gm, (off0, route0)):
+        if it in sample:
+            ids, delta, flags, chosen = oracle.eval_neighbourhood(pb, off, route, tabu, it, zb)
+            assert int(gm[it]) == (0xFFFFFFFF if chosen < 0 else int(ids[chosen])), f"iteration {it}"
+        if it > 0:
+            assert int(gz[it - 1]) == z, f"objective after iteration {it - 1}"
+    assert int(gz[-1]) == oracle.cost(pb, off, route)[0]
+    zs = np.concatenate([[info[api.INFO_Z_INIT]], gz])
+    assert info[api.INFO_Z_BEST] == zs.min()
+    assert info[api.INFO_BEST_IT] == int(np.argmin(zs)) - 1
+    z, fl, ov = oracle.cost(pb, out.route_off.cpu().numpy()[: pb.V + 1], out.route.cpu().numpy()[: pb.M])
+    assert z == info[api.INFO_Z_BEST]
+    np.testing.assert_array_equal(out.flight.cpu().numpy()[: pb.V], fl)
+    np.testing.assert_array_equal(out.overflow.cpu().numpy()[: pb.V], ov)
+
+
+def test_large_grid_equals_one_cluster():
+    """The large instance on every cluster of the device (asched_tabu_solve) and on one
+    cluster (asched_solve): identical trajectories and outputs."""
+    inst, p = gen.large(0), gen.LARGE_PARAMS
+    dp = api.DeviceProblem(inst)
+    params = api.params_from(p, iterations=400)
+    a = api.solve(dp, params, trajectory=True)
+    b = api.solve_one_cluster(dp, params, trajectory=True)
+    torch.cuda.synchronize()
+    assert int(a.info[api.INFO_STATUS]) == 0
+    for k in ("route_off", "route", "flight", "overflow", "info", "traj_move", "traj_z"):
+        assert torch.equal(getattr(a, k), getattr(b, k)), k
 
 
 def test_device_status_codes():
@@ -385,17 +464,18 @@ def test_host_side_errors():
     assert int(out.info[api.INFO_STATUS]) == api.E_TOO_LARGE
 
 
-@pytest.mark.parametrize("cluster", [2, 16])
-def test_bounded_wait_reports_timeout_and_context_stays_usable(cluster):
-    """A CTA that never publishes its key (test hook) makes every peer's bounded wait run
-    out: the call ends with ASCHED_E_TIMEOUT, and the next solve in the same context is
-    correct."""
+@pytest.mark.parametrize("cluster,grid", [(2, 1), (16, 1), (2, 3), (1, 4), (16, 2)])
+def test_bounded_wait_reports_timeout_and_context_stays_usable(cluster, grid):
+    """A CTA (one cluster) or a cluster (several) that never publishes its key (test hook)
+    makes every other bounded wait run out: the call ends with ASCHED_E_TIMEOUT, and the
+    next solve in the same context is correct."""
     inst = gen.random_instance(95, n_loc=10, n_vehicles=4, n_missions=30, duty_cap=2000)
     dp = api.DeviceProblem(inst)
-    params = api.make_params(4, 50, PENALTY, 1000, cluster_size=cluster, timeout_ns=50_000_000)
+    params = api.make_params(4, 50, PENALTY, 1000, cluster_size=cluster, timeout_ns=50_000_000,
+                             grid_clusters=grid)
     params.flags |= api._lib.TEST_WITHHOLD_KEY
     out = api.solve(dp, params)
     torch.cuda.synchronize()
     assert int(out.info[api.INFO_STATUS]) == api.E_TIMEOUT
     assert int(out.info[api.INFO_ITERS]) == 0
-    _check_solve_vs_oracle(inst, PENALTY, 4, 50, cluster_size=cluster)
+    _check_solve_vs_oracle(inst, PENALTY, 4, 50, cluster_size=cluster, grid_clusters=grid)

@@ -1,11 +1,13 @@
 """The request server (asched_serve + serve.Server): every request's result equals the
-result of solving it alone, however requests overlap on the device (needs a GB300)."""
+CPU oracle's and the result of solving it alone, however requests overlap on the device
+(needs a GB300)."""
 import time
 
 import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2002_11710_gb300 import api, gen, serve
 from paper_2002_11710_gb300._lib import CTRL_IDLE_EXITS
 
@@ -32,6 +34,87 @@ def _compare(got, want, V, M):
     np.testing.assert_array_equal(got["flight"][:V], want["flight"])
     np.testing.assert_array_equal(got["overflow"][:V], want["overflow"])
     return True
+
+
+def _compare_oracle(got, inst, mode, tenure, iterations):
+    """A served result against the oracle's Tabu search of the same instance."""
+    pb = oracle.Problem(inst, mode, 1000)
+    r = oracle.tabu_search(pb, tenure, iterations)
+    V, M = inst.n_vehicles, inst.n_missions
+    if r["status"] != 0:
+        assert got["info"][api.INFO_STATUS] == r["status"]
+        return False
+    assert got["info"][api.INFO_STATUS] == 0
+    assert got["info"][api.INFO_Z_BEST] == r["z_best"]
+    assert got["info"][api.INFO_BEST_IT] == r["best_it"]
+    assert got["info"][api.INFO_ITERS] == iterations
+    if iterations:
+        assert got["info"][api.INFO_Z_FINAL] == r["traj_z"][-1]
+    np.testing.assert_array_equal(got["route_off"][: V + 1], r["route_off"])
+    np.testing.assert_array_equal(got["route"][:M], r["route"])
+    z, fl, ov = oracle.cost(pb, r["route_off"], r["route"])
+    np.testing.assert_array_equal(got["flight"][:V], fl)
+    np.testing.assert_array_equal(got["overflow"][:V], ov)
+    rc, off0, route0 = oracle.greedy_init(pb)
+    assert got["info"][api.INFO_Z_INIT] == oracle.cost(pb, off0, route0)[0]
+    return True
+
+
+@pytest.mark.parametrize("compact", [False, True], ids=["tables", "int16"])
+def test_served_results_equal_the_oracle(compact):
+    """Requests of mixed sizes (two vehicle types, heli-only missions) streamed through both
+    lanes of the server (one CTA per request below 30 missions, 4-CTA clusters from 30 up)
+    with fewer slots than requests: every served result equals the oracle's search of that
+    request (best schedule, objective, best iteration, flights, overflow). Run in both
+    shared-memory layouts, so the cluster lane covers the int16 matrix too."""
+    reqs = [gen.random_instance(1300 + k, n_loc=6 + k % 11, n_vehicles=1 + k % 7, n_missions=3 + (17 * k) % 58,
+                                n_types=2, heli_only_frac=0.25 if k % 3 else 0.0, duty_cap=1500,
+                                max_minutes=120) for k in range(28)]
+    n_big = sum(r.n_missions >= 30 for r in reqs)
+    assert 5 <= n_big <= len(reqs) - 5
+    tenure, iters = 5, 120
+    params = api.make_params(tenure, iters, gen.PENALTY, 1000, compact=compact)
+    srv = serve.Server(max_loc=16, max_vehicles=8, max_missions=64, n_types=2, n_slots=6,
+                       big_missions=30, big_cluster=4, big_clusters=2)
+    got = {}
+    srv.start(params, idle_timeout_s=30.0, max_ctas=12)
+    try:
+        arrivals = np.cumsum(np.random.default_rng(3).exponential(0.0003, size=len(reqs)))
+        serve.run_stream(srv, reqs, arrivals, on_done=lambda i, s: got.__setitem__(i, srv.result(s)))
+    finally:
+        srv.stop()
+    assert sorted(got) == list(range(len(reqs)))
+    assert int(srv.control_big[api._lib.CTRL_SERVED].item()) == n_big
+    # every status equals the oracle's; the requests whose greedy start exists (all but the
+    # two whose heli-only missions have no helicopter) equal it in every output
+    solved = sum(_compare_oracle(got[i], inst, gen.PENALTY, tenure, iters) for i, inst in enumerate(reqs))
+    assert solved == len(reqs) - 2
+
+
+def test_serving_workload_sample_equals_the_oracle():
+    """A short stream of the serving workload (lognormal sizes, 1,000 iterations) with the
+    cluster lane for requests of 60 missions or more: a sample of served results from
+    both lanes equals the oracle's search."""
+    arrivals = gen.poisson_arrivals(8, 2000.0, 0.05)
+    reqs = [gen.serving_request(13_000 + k) for k in range(len(arrivals))]
+    p = gen.SERVING_PARAMS
+    params = api.params_from(p)
+    srv = serve.Server(max_loc=72, max_vehicles=80, max_missions=400, n_slots=128, big_missions=60,
+                       big_cluster=8, big_clusters=4)
+    small = [i for i, r in enumerate(reqs) if r.n_missions < 60][:3]
+    big = [i for i, r in enumerate(reqs) if r.n_missions >= 60][:2]
+    assert small and big
+    keep = set(small + big)
+    got = {}
+    srv.start(params, idle_timeout_s=30.0)
+    try:
+        serve.run_stream(srv, reqs, arrivals,
+                         on_done=lambda i, s: got.__setitem__(i, srv.result(s)) if i in keep else None)
+    finally:
+        srv.stop()
+    assert srv.served() == len(reqs)
+    for i in sorted(keep):
+        assert _compare_oracle(got[i], reqs[i], p.cap_mode, p.tenure, p.iterations), i
 
 
 def test_served_results_equal_solving_alone_with_few_slots():

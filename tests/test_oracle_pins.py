@@ -292,3 +292,34 @@ def test_infeasible_init_reported():
     pb = oracle.Problem(inst, ilp.HARD, 1000)
     rc, _, _ = oracle.greedy_init(pb)
     assert rc == oracle.E_INFEASIBLE_INIT
+
+
+def test_thread_count_does_not_change_results():
+    """The loop over moves runs on OpenMP threads; the chosen move is picked afterwards in
+    canonical order, so per-move deltas, flags and whole trajectories are the same on one
+    thread and on every core."""
+    import oracle
+
+    inst = gen.random_instance(49, n_loc=12, n_vehicles=6, n_missions=23, n_types=2, heli_only_frac=0.25,
+                               deadlines=True, deadline_lo=1000, duty_cap=2500, max_minutes=60)
+    pb = oracle.Problem(inst, gen.PENALTY, 1000)
+    runs = []
+    before = oracle.set_threads(0)
+    try:
+        for threads in (1, 3, 0):
+            oracle.set_threads(threads if threads else before)
+            r = oracle.tabu_search(pb, 4, 40)
+            rc, off, route = oracle.greedy_init(pb)
+            tabu = np.random.default_rng(1).integers(-1, 5, size=(pb.M, pb.V)).astype(np.int32)
+            ev = oracle.eval_neighbourhood(pb, off, route, tabu, 2, oracle.cost(pb, off, route)[0] - 5)
+            runs.append((r, ev))
+    finally:
+        oracle.set_threads(before)
+    (r0, e0) = runs[0]
+    assert r0["status"] == 0
+    for r, e in runs[1:]:
+        np.testing.assert_array_equal(r["traj_move"], r0["traj_move"])
+        np.testing.assert_array_equal(r["traj_z"], r0["traj_z"])
+        for a, b in zip(e[:3], e0[:3]):
+            np.testing.assert_array_equal(a, b)
+        assert e[3] == e0[3]

@@ -61,11 +61,13 @@ def test_golden_line_sweep():
 
 
 # (seed, n_loc, V, M, n_types, heli-only fraction, deadlines, duty cap)
+# Seeds chosen so that Algorithm 1 finds a feasible start in both cap modes (a case
+# without one would test nothing but the error).
 CASES = [
-    (11, 6, 2, 4, 1, 0.0, False, 400),
+    (17, 6, 2, 4, 1, 0.0, False, 400),
     (12, 7, 3, 5, 2, 0.4, False, 500),
     (13, 8, 3, 6, 2, 0.3, True, 900),
-    (14, 9, 4, 7, 2, 0.3, False, 350),
+    (20, 9, 4, 7, 2, 0.3, False, 350),
     (15, 10, 4, 9, 2, 0.25, True, 1200),
     (16, 12, 5, 11, 2, 0.2, False, 600),
 ]
@@ -208,8 +210,7 @@ def test_sweeps_rederived_by_brute_force(case, mode):
     inst = _inst(case)
     pb = oracle.Problem(inst, mode, 1000)
     rc, off, route = oracle.greedy_init(pb)
-    if rc != 0:
-        pytest.skip("greedy start infeasible for this case")
+    assert rc == 0, "every case has a feasible greedy start"
     for name, run, is_tabu, tenure, aw in _variants():
         r = run(pb)
         assert r["status"] == 0, name
@@ -230,8 +231,7 @@ def test_trace_replays_on_feasible_schedules(case, mode):
     inst = _inst(case)
     pb = oracle.Problem(inst, mode, 1000)
     rc, off, route = oracle.greedy_init(pb)
-    if rc != 0:
-        pytest.skip("greedy start infeasible for this case")
+    assert rc == 0, "every case has a feasible greedy start"
     M = inst.n_missions
     for name, run, is_tabu, tenure, aw in _variants():
         r = run(pb)
@@ -384,8 +384,7 @@ def test_sweeps_with_random_orders_rederived(case, mode):
     inst = _inst(case)
     pb = oracle.Problem(inst, mode, 1000)
     rc, off, route = oracle.greedy_init(pb)
-    if rc != 0:
-        pytest.skip("greedy start infeasible for this case")
+    assert rc == 0, "every case has a feasible greedy start"
     for seed in range(3):
         vo, mr = gen.sweep_orders(seed, inst.n_vehicles, inst.n_missions)
         for is_tabu, tenure, aw in ((False, 0, False), (True, 3, False), (True, 3, True)):
