@@ -271,7 +271,8 @@ def time_single(name, args, dev, world, flush, barrier, clocks=None):
     inst, p = workload(name)
     M, V = inst.n_missions, inst.n_vehicles
     R, S = moves_split(M, V)
-    params = api.params_from(p, cluster_size=args.cluster, block_threads=args.threads, grid_clusters=args.grid)
+    params = api.params_from(p, cluster_size=args.cluster, block_threads=args.threads, grid_clusters=args.grid,
+                             plain_launch=args.plain_launch)
     dp = api.DeviceProblem(inst, dev)
     plan = api.plan(dp, params)
     out = api.alloc_output(dp, p.iterations)
@@ -679,6 +680,8 @@ def main():
     ap.add_argument("--cluster", type=int, default=0, help="CTAs per cluster (0: the plan's)")
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: the plan's)")
     ap.add_argument("--grid", type=int, default=0, help="clusters per instance (0: the plan's)")
+    ap.add_argument("--plain-launch", action="store_true",
+                    help="launch several clusters without the cooperative attribute (for ncu)")
     ap.add_argument("--cpu-iterations", type=int, default=8,
                     help="iterations of the one-core oracle sample (0 skips the CPU baselines)")
     ap.add_argument("--cpu-iterations-all", type=int, default=60,

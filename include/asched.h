@@ -116,8 +116,8 @@ typedef struct {
  *                       on it.
  *   block_threads       0 = automatic, else a multiple of 32 in [64, 512].
  *   timeout_ns          bound on every wait between CTAs; 0 = 1 s.
- *   flags               0, or a combination of ASCHED_COMPACT_LAYOUT and
- *                       ASCHED_TEST_WITHHOLD_KEY.
+ *   flags               0, or a combination of ASCHED_COMPACT_LAYOUT,
+ *                       ASCHED_TEST_WITHHOLD_KEY and ASCHED_PLAIN_LAUNCH.
  *   grid_clusters       clusters cooperating on one instance in asched_tabu_solve: 0 =
  *                       automatic, else 1..1024, every cluster resident at once (else
  *                       ASCHED_E_TOO_LARGE). Neighbourhoods of more than 4 chunks of 32
@@ -139,6 +139,12 @@ typedef struct {
  * timeout_ns and the call reports ASCHED_E_TIMEOUT (nothing faults or hangs). No effect
  * with one CTA. */
 #define ASCHED_TEST_WITHHOLD_KEY 2u
+/* Launch the clusters of a multi-cluster search (grid_clusters > 1) without the
+ * cooperative attribute, for tools that cannot replay a cooperative cluster launch (a
+ * profiler). Co-residency of the clusters is then not guaranteed: on a device busy with
+ * other work, a cluster that cannot start in time makes the others' bounded waits run
+ * out (ASCHED_E_TIMEOUT). Results are unchanged. */
+#define ASCHED_PLAIN_LAUNCH 4u
 typedef struct {
   int32_t tenure;
   int32_t iterations;
@@ -234,8 +240,10 @@ int asched_solve(const asched_instance* inst, const asched_params* params,
  *                          memory of at least asched_workspace_bytes, 128-byte aligned
  *                          (NULL and 0 when that is 0); the call zeroes it on `stream`
  *                          before the launch, and two searches in flight at once need
- *                          two workspaces. The launch is cooperative, so every cluster is
- *                          resident at once; it fails with ASCHED_E_CUDA otherwise.
+ *                          two workspaces. The launch is cooperative (unless
+ *                          ASCHED_PLAIN_LAUNCH), so every cluster is resident at once; it
+ *                          fails with ASCHED_E_CUDA otherwise. A kernel launched with
+ *                          another shape than planned writes ASCHED_E_INVALID and returns.
  *                          Results equal asched_solve's bit for bit. */
 int asched_validate(const asched_instance* inst, const asched_params* params);
 int asched_workspace_bytes(const asched_instance* inst, const asched_params* params, size_t* bytes);

@@ -26,6 +26,7 @@ HARD = 0
 PENALTY = 1
 COMPACT_LAYOUT = 1  # asched_params.flags bits
 TEST_WITHHOLD_KEY = 2
+PLAIN_LAUNCH = 4
 
 FLAG_FEASIBLE, FLAG_TABU, FLAG_ASPIRATION, FLAG_ADMISSIBLE = 1, 2, 4, 8
 SWAP_BIT = 0x80000000

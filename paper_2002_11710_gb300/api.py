@@ -34,13 +34,14 @@ def num_moves(n_missions: int, n_vehicles: int) -> int:
 
 def make_params(tenure: int, iterations: int, cap_mode: int = HARD, lam: int = 1000,
                 cluster_size: int = 0, block_threads: int = 0, timeout_ns: int = 0,
-                compact: bool = False, grid_clusters: int = 0) -> _lib.Params:
+                compact: bool = False, grid_clusters: int = 0, plain_launch: bool = False) -> _lib.Params:
     """compact: keep the travel matrix as int16 in shared memory instead of the gather
     tables (used automatically when the tables do not fit). grid_clusters: clusters
-    cooperating on one instance (0 = automatic)."""
+    cooperating on one instance (0 = automatic). plain_launch: launch several clusters
+    without the cooperative attribute (for profilers)."""
+    flags = (_lib.COMPACT_LAYOUT if compact else 0) | (_lib.PLAIN_LAUNCH if plain_launch else 0)
     return _lib.Params(int(tenure), int(iterations), int(cap_mode), int(lam), int(cluster_size),
-                       int(block_threads), int(timeout_ns), _lib.COMPACT_LAYOUT if compact else 0,
-                       int(grid_clusters))
+                       int(block_threads), int(timeout_ns), flags, int(grid_clusters))
 
 
 def params_from(p, **overrides) -> _lib.Params:

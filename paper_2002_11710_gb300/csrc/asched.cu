@@ -173,6 +173,22 @@ __device__ __forceinline__ uint32_t cluster_rank() {
   return r;
 }
 
+// CTAs in this CTA's cluster as launched (1 without a cluster launch).
+__device__ __forceinline__ uint32_t cluster_ctas() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+
+// The launch has the shape the parameters describe: C CTAs per cluster and `ctas` CTAs
+// in all, in a one-dimensional grid. Kernels check this before any access to a peer's
+// shared memory, whose address would not exist in a launch of another shape (for
+// instance one replayed without its cluster attribute).
+__device__ __forceinline__ bool launch_shape_ok(int C, int ctas) {
+  return static_cast<int>(cluster_ctas()) == C && (ctas <= 0 || static_cast<int>(gridDim.x) == ctas) &&
+         gridDim.y == 1 && gridDim.z == 1;
+}
+
 __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
                    : "memory");
@@ -201,6 +217,11 @@ __device__ __forceinline__ int ld_peer_i32(uint32_t cluster_addr) {
   int v;
   asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(cluster_addr) : "memory");
   return v;
+}
+
+// Store into this CTA's shared memory for its other warps (relaxed, CTA scope).
+__device__ __forceinline__ void st_own_u64(uint32_t cta_addr, uint64_t v) {
+  asm volatile("st.relaxed.cta.shared::cta.u64 [%0], %1;" ::"r"(cta_addr), "l"(v) : "memory");
 }
 
 // Load from this CTA's shared memory, observing peers' relaxed stores.
@@ -1101,19 +1122,23 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
       }
       if (K > 1) {
         // Between clusters: rank 0 of each cluster stores the cluster's key, tagged, into
-        // global slot [it & 1][cid]; its warp 0 polls the K slots until all carry this
-        // iteration's tag (bounded), takes the least and pushes it, tagged, into every CTA
-        // of its cluster; every warp polls its own copy. A wait that gives up is pushed as
-        // a key with kFailBit. The slots were zeroed before the launch; a slot buffer is
-        // reused two iterations later, when every cluster has read it (a cluster publishes
-        // for it + 1 only after reading all keys of it).
+        // global slot [it & 1][cid]; warp 0 of every CTA polls the K slots until all carry
+        // this iteration's tag (bounded), takes the least and stores it, tagged, into its
+        // own CTA's shared memory, where every warp polls it. A wait that gives up is
+        // stored as a key with kFailBit. (Every CTA polling L2 itself measured faster than
+        // rank 0 polling and pushing the key to its peers over DSMEM; more polling warps
+        // per CTA, or every CTA publishing its own key, slower.) The slots were zeroed
+        // before the launch; a slot buffer is reused two iterations later, when every CTA
+        // has read it (a cluster publishes for it + 1 only after its CTAs have read all
+        // keys of it, the cluster exchange of it + 1 coming first).
         const int sb = it & 1;
         const uint64_t tag = iter_tag(it);
         const uint32_t gk_addr = smem_u32(&sm.gkey()[sb]);
-        if (rank == 0 && warp == 0) {
+        if (warp == 0) {
           uint64_t* gs = P.gslots + static_cast<int64_t>(sb) * P.gslot_stride;
           const bool withhold = P.test_withhold && it == 0 && cid == K - 1;  // test hook
-          if (lane == 0 && !timed_out && !withhold) st_relaxed_gpu_u64(gs + cid, (gk & ~(kTagMask | kFailBit)) | tag);
+          if (rank == 0 && lane == 0 && !timed_out && !withhold)
+            st_relaxed_gpu_u64(gs + cid, (gk & ~(kTagMask | kFailBit)) | tag);
           bool ok = !timed_out;
           uint64_t m = kNoKey;
           if (ok) {
@@ -1137,7 +1162,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
             }
           }
           const uint64_t msg = ok ? ((m & ~kTagMask) | tag) : ((0xFFFFFFFFull << 32) | kFailBit | tag);
-          if (lane < C) st_peer_u64(mapa_rank(gk_addr, lane), msg);
+          if (lane == 0) st_own_u64(gk_addr, msg);
         }
         if (!timed_out) {
           uint64_t v = ld_own_u64(gk_addr);
@@ -1378,8 +1403,12 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
 template <bool PEN, bool DL, bool DEBUG, bool BIG>
 __global__ void __launch_bounds__(kMaxThreads, 1) tabu_kernel(const __grid_constant__ KParams P) {
   const int C = P.cluster;
+  const int K = P.grid_clusters > 1 ? P.grid_clusters : 1;
+  if (!launch_shape_ok(C, K * C)) {  // uniform over the launch: every CTA returns here
+    if (blockIdx.x == 0 && threadIdx.x == 0 && P.info) P.info[ASCHED_INFO_STATUS] = ASCHED_E_INVALID;
+    return;
+  }
   const int rank = C > 1 ? static_cast<int>(cluster_rank()) : 0;
-  const int K = P.grid_clusters;
   const int cid = K > 1 ? static_cast<int>(blockIdx.x) / C : 0;
   solve_one<PEN, DL, DEBUG, BIG, false>(P, P.lay, C, rank, K, cid);
 }
@@ -1514,6 +1543,7 @@ template <bool PEN, bool DL, bool CL>
 __global__ void __launch_bounds__(kMaxThreads, 1) serve_kernel(const __grid_constant__ SParams Q) {
   __shared__ int s_ticket;
   const int C = CL ? Q.run.cluster : 1;
+  if (CL && !launch_shape_ok(C, 0)) return;  // uniform over the launch; nothing is served
   const int rank = CL ? static_cast<int>(cluster_rank()) : 0;
   if (threadIdx.x == 0) atomicAdd(&Q.control[ASCHED_CTRL_STARTED], 1);
   uint64_t idle_since = global_ns();
@@ -1654,7 +1684,7 @@ int check_sizes(const asched_instance* inst, const asched_params* p) {
     return ASCHED_E_INVALID;
   if (p->block_threads != 0 && (p->block_threads < 64 || p->block_threads > kMaxThreads || p->block_threads % 32))
     return ASCHED_E_INVALID;
-  if (p->timeout_ns < 0 || (p->flags & ~(ASCHED_COMPACT_LAYOUT | ASCHED_TEST_WITHHOLD_KEY)) != 0)
+  if (p->timeout_ns < 0 || (p->flags & ~(ASCHED_COMPACT_LAYOUT | ASCHED_TEST_WITHHOLD_KEY | ASCHED_PLAIN_LAUNCH)) != 0)
     return ASCHED_E_INVALID;
   if (p->grid_clusters < 0 || p->grid_clusters > kMaxGridClusters) return ASCHED_E_INVALID;
   return ASCHED_OK;
@@ -1862,7 +1892,7 @@ int launch(const asched_instance* inst, const asched_params* p, bool debug, KPar
   attr[1].id = cudaLaunchAttributeCooperative;
   attr[1].val.cooperative = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = K > 1 ? 2 : 1;
+  cfg.numAttrs = (K > 1 && !(p->flags & ASCHED_PLAIN_LAUNCH)) ? 2 : 1;
   void* args[] = {&kp};
   if (cudaLaunchKernelExC(&cfg, fn, args) != cudaSuccess) {
     (void)cudaGetLastError();

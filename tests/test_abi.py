@@ -86,7 +86,7 @@ def test_check_instance_host_rejects_bad_params():
     assert api.check_instance_host(inst, _params(cluster_size=16, block_threads=64)) == api.OK
     assert api.check_instance_host(inst, _params(compact=True)) == api.OK
     p = _params()
-    p.flags = 4
+    p.flags = 8
     assert api.check_instance_host(inst, p) == api.E_INVALID
 
 

@@ -398,6 +398,14 @@ def test_large_full_run_sampled_against_oracle():
     np.testing.assert_array_equal(out.overflow.cpu().numpy()[: pb.V], ov)
 
 
+def test_plain_launch_gives_the_same_trajectory():
+    """ASCHED_PLAIN_LAUNCH (no cooperative attribute) changes nothing in the results."""
+    inst = gen.random_instance(51, n_loc=14, n_vehicles=8, n_missions=40, n_types=2,
+                               heli_only_frac=0.2, duty_cap=900, max_minutes=120)
+    _check_solve_vs_oracle(inst, PENALTY, 6, 80, cluster_size=4, block_threads=128, grid_clusters=5,
+                           plain_launch=True)
+
+
 def test_large_grid_equals_one_cluster():
     """The large instance on every cluster of the device (asched_tabu_solve) and on one
     cluster (asched_solve): identical trajectories and outputs."""
