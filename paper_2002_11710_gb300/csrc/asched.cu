@@ -22,8 +22,10 @@
 //   * The schedule is a doubly linked list over nodes (missions 0..M-1 and route
 //     ends M..M+V-1), with per-node records (removal delta, gap leg, slot cost,
 //     table row offsets, cap slack, deadline slacks) in a double-buffered SoA.
-//     Applying a move rewrites every node's record from the previous buffer in one
-//     pass (one thread per node), so apply and preparation need no barrier between.
+//     Applying a move writes the other buffer in one pass (one thread per node) with
+//     no barrier between decode and write: a node's records depend only on its own
+//     route, so only the nodes of the one or two routes the move changes are
+//     recomputed; those the previous move changed are copied; the rest are current.
 //   * Every move (relocate (m, y) and swap (a, b)) is evaluated in O(1) from the
 //     records and the tables; the per-thread, warp (redux.sync), CTA (shared
 //     memory) and cluster (DSMEM) minimum of the key ((delta ^ 2^31) << 32) | id
@@ -659,6 +661,44 @@ __device__ __forceinline__ uint64_t eval_swap(const Smem& sm, const Tab<BIG>& tb
   return adm ? pack_key(delta, id) : kNoKey;
 }
 
+// Flight after move `id` of the source route (src) or of the target route (!src): the
+// route's flight from FB plus the move's change of it, from the same records and table
+// entries the evaluators use. A move inside one route changes it by the whole delta.
+template <bool BIG>
+__device__ __forceinline__ int moved_flight(const Smem& sm, const Tab<BIG>& tb, const State& S, const Ctx& c,
+                                            uint32_t id, bool src) {
+  if (!(id & kSwapBit)) {
+    const int m = static_cast<int>(id >> kIdShift), y = static_cast<int>(id & kIdMask);
+    const int2 r = S.r2()[m];
+    const int4 g = S.y4()[y];
+    const int va = nv_veh(r.x), vb = nv_veh(g.w);
+    const int ins = tb.a(g.x, m) + tb.b(g.y, m) - g.z;
+    const int f = S.fb()[src ? va : vb] + c.cap;
+    if (va == vb) return f + r.y + ins;
+    return src ? f + r.y : f + ins;
+  }
+  const int a = static_cast<int>((id >> kIdShift) & kIdMask), b = static_cast<int>(id & kIdMask);
+  const SwapParts q = swap_parts<BIG>(sm, tb, S, c, a, b);
+  const int va = nv_veh(q.sa.x), vb = nv_veh(q.sb.x);
+  const int da = q.t1 + q.t2 - q.sa.w;
+  const int db = q.t3 + q.t4 - q.sb.w;
+  const int f = S.fb()[src ? va : vb] + c.cap;
+  if (va == vb) return f + da + db;
+  return src ? f + da : f + db;
+}
+
+// Copy every record of node t from buffer S to buffer S2 (t's route is unchanged).
+template <bool DL, bool RP>
+__device__ __forceinline__ void copy_records(const State& S, const State& S2, const Ctx& c, int t) {
+  S2.r2()[t] = S.r2()[t];
+  S2.y4()[t] = S.y4()[t];
+  S2.s4()[t] = S.s4()[t];
+  if (DL) S2.d4()[t] = S.d4()[t];
+  S2.prv()[t] = S.prv()[t];
+  if (t >= c.M) S2.fb()[t - c.M] = S.fb()[t - c.M];
+  if (RP && t < c.M) S2.rp()[t] = S.rp()[t];
+}
+
 // ------------------------------------------------------------------ the kernel -----
 
 // The compact layout's int16 matrix, row t*L + r of layer t at T16 + (t*L + r) * Ls, zero
@@ -1024,6 +1064,8 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
 
   // ---- main loop
   int zbest = Z, best_it = -1, it = 0, cur = 0;
+  int pva = -1, pvb = -1;  // vehicles of the last applied move
+  bool first_move = true;
   const bool looped = status == ASCHED_OK;  // uniform over the cluster
   if (looped) {
     if (C > 1) cluster_sync_all();
@@ -1200,64 +1242,37 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
       if (DEBUG) {
         if (lead && tid == 0 && !timed_out) *P.dbg_key = gk;
       } else if (!timed_out && !bad_key && gk != kNoKey) {
-        // ---- apply the chosen move: every thread decodes it from the current buffer,
-        // then rewrites the records of its nodes into the other buffer.
+        // ---- apply the chosen move. Records go into the other buffer, and a node's
+        // records depend only on its own route, so only the nodes of the one or two routes
+        // the move changes (vehicles va, vb) are recomputed there; the nodes the previous
+        // applied move changed (vehicles pva, pvb), stale in that buffer, are copied over;
+        // every other node's records there are current already. Before the first applied
+        // move the other buffer holds nothing, so every node is copied.
         const State S2 = sm.st(cur ^ 1);
         const int Znew = Z + key_delta(gk);
         const bool improved = Znew < zbest;
-        if (warp * 32 < N) {  // only warps that own nodes need the decoded move
-          const uint32_t id = static_cast<uint32_t>(gk);
-          const bool is_swap = (id & kSwapBit) != 0;
-          int m = 0, y = 0, e = 0, s = 0, x = 0, a = 0, b = 0, pa = 0, na = 0, pb = 0, nb = 0;
-          bool adjA = false, adjB = false;
-          int vwa, vwb, fa2, fb2 = 0;
-          if (!is_swap) {
-            m = static_cast<int>(id >> kIdShift);
-            y = static_cast<int>(id & kIdMask);
-            const int2 r = S.r2()[m];
-            const int4 g = S.y4()[y];
-            vwa = nv_vw(r.x);
-            vwb = nv_vw(g.w);
-            s = nv_next(r.x);
-            e = S.prv()[m];
-            x = S.prv()[y];
-            const int ins = tb.a(g.x, m) + tb.b(g.y, m) - g.z;
-            const int fa = S.fb()[vw_veh(vwa)] + c.cap;
-            if (vw_veh(vwa) == vw_veh(vwb)) {
-              fa2 = fa + r.y + ins;
-            } else {
-              fa2 = fa + r.y;
-              fb2 = S.fb()[vw_veh(vwb)] + c.cap + ins;
-            }
-          } else {
-            a = static_cast<int>((id >> kIdShift) & kIdMask);
-            b = static_cast<int>(id & kIdMask);
-            const SwapParts q = swap_parts<BIG>(sm, tb, S, c, a, b);
-            vwa = nv_vw(q.sa.x);
-            vwb = nv_vw(q.sb.x);
-            na = nv_next(q.sa.x);
-            nb = nv_next(q.sb.x);
-            pa = S.prv()[a];
-            pb = S.prv()[b];
-            adjA = q.adjA;
-            adjB = q.adjB;
-            const int da = q.t1 + q.t2 - q.sa.w;
-            const int db = q.t3 + q.t4 - q.sb.w;
-            const int fa = S.fb()[vw_veh(vwa)] + c.cap;
-            if (vw_veh(vwa) == vw_veh(vwb)) {
-              fa2 = fa + da + db;
-            } else {
-              fa2 = fa + da;
-              fb2 = S.fb()[vw_veh(vwb)] + c.cap + db;
-            }
-          }
-          const int va = vw_veh(vwa), vb = vw_veh(vwb);
-          for (int t = tid; t < N; t += nthr) {
-            const int nv = S.nv(t);
-            int nx = nv_next(nv), pv = S.prv()[t], vw = nv_vw(nv);
-            if (!is_swap) {
-              if (t == e) nx = s;
-              if (t == s) pv = e;
+        const uint32_t id = static_cast<uint32_t>(gk);
+        const bool is_swap = (id & kSwapBit) != 0;
+        // the move's nodes and links (relocation: m = n1 before y = n2; swap: a = n1, b = n2)
+        const int n1 = static_cast<int>(is_swap ? ((id >> kIdShift) & kIdMask) : (id >> kIdShift));
+        const int n2 = static_cast<int>(id & kIdMask);
+        const int nv1 = S.nv(n1), nv2 = S.nv(n2);
+        const int p1 = S.prv()[n1], p2 = S.prv()[n2];
+        const int vwa = nv_vw(nv1), vwb = nv_vw(nv2);
+        const int va = vw_veh(vwa), vb = vw_veh(vwb);
+        const int x1 = nv_next(nv1), x2 = nv_next(nv2);
+        const bool adjA = is_swap && x1 == n2;  // a immediately before b
+        const bool adjB = is_swap && x2 == n1;  // b immediately before a
+        for (int t = tid; t < N; t += nthr) {
+          const int nv = S.nv(t);
+          const int vt = nv_veh(nv);
+          int nx = nv_next(nv);
+          if (vt == va || vt == vb) {
+            int pv = S.prv()[t], vw = nv_vw(nv);
+            if (!is_swap) {  // e -> m -> s ... x -> y  becomes  e -> s ... x -> m -> y
+              const int m = n1, y = n2, e = p1, sx = x1, x = p2;
+              if (t == e) nx = sx;
+              if (t == sx) pv = e;
               if (t == x) nx = m;
               if (t == y) pv = m;
               if (t == m) {
@@ -1265,58 +1280,64 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
                 pv = x;
                 vw = vw_move(vwb, vw);
               }
-            } else if (adjA) {  // pa -> a -> b -> nb  becomes  pa -> b -> a -> nb
-              if (t == pa) nx = b;
-              if (t == nb) pv = a;
-              if (t == b) {
-                pv = pa;
-                nx = a;
-              }
-              if (t == a) {
-                pv = b;
-                nx = nb;
-              }
-            } else if (adjB) {  // pb -> b -> a -> na  becomes  pb -> a -> b -> na
-              if (t == pb) nx = a;
-              if (t == na) pv = b;
-              if (t == a) {
-                pv = pb;
-                nx = b;
-              }
-              if (t == b) {
-                pv = a;
-                nx = na;
-              }
             } else {
-              if (t == pa) nx = b;
-              if (t == na) pv = b;
-              if (t == pb) nx = a;
-              if (t == nb) pv = a;
-              if (t == a) {
-                pv = pb;
-                nx = nb;
-                vw = vw_move(vwb, vwa);
-              }
-              if (t == b) {
-                pv = pa;
-                nx = na;
-                vw = vw_move(vwa, vwb);
+              const int a = n1, b = n2, pa = p1, na = x1, pb = p2, nb = x2;
+              if (adjA) {  // pa -> a -> b -> nb  becomes  pa -> b -> a -> nb
+                if (t == pa) nx = b;
+                if (t == nb) pv = a;
+                if (t == b) {
+                  pv = pa;
+                  nx = a;
+                }
+                if (t == a) {
+                  pv = b;
+                  nx = nb;
+                }
+              } else if (adjB) {  // pb -> b -> a -> na  becomes  pb -> a -> b -> na
+                if (t == pb) nx = a;
+                if (t == na) pv = b;
+                if (t == a) {
+                  pv = pb;
+                  nx = b;
+                }
+                if (t == b) {
+                  pv = a;
+                  nx = na;
+                }
+              } else {
+                if (t == pa) nx = b;
+                if (t == na) pv = b;
+                if (t == pb) nx = a;
+                if (t == nb) pv = a;
+                if (t == a) {
+                  pv = pb;
+                  nx = nb;
+                  vw = vw_move(vwb, vwa);
+                }
+                if (t == b) {
+                  pv = pa;
+                  nx = na;
+                  vw = vw_move(vwa, vwb);
+                }
               }
             }
-            const int vv = vw_veh(vw);
-            const int f2 = vv == va ? fa2 : (vv == vb ? fb2 : S.fb()[vv] + c.cap);
+            // The new flight of t's route is needed by route ends (FB) and, with RP
+            // records, by every mission.
+            int f2 = 0;
+            if (RP || t >= M) f2 = moved_flight<BIG>(sm, tb, S, c, id, vw_veh(vw) == va);
             write_records<PEN, DL, BIG, RP>(sm, tb, S2, c, t, nx, pv, vw, f2);
-            if (improved) sm.best[t] = nx;
+          } else if (first_move || vt == pva || vt == pvb) {
+            copy_records<DL, RP>(S, S2, c, t);
           }
-          if (tid == 0) {
-            if (!is_swap) {
-              tb.set_tabu(va, m, it + P.tenure);
-            } else {
-              tb.set_tabu(va, a, it + P.tenure);
-              tb.set_tabu(vb, b, it + P.tenure);
-            }
-          }
+          if (improved) sm.best[t] = nx;
         }
+        if (tid == 0) {
+          tb.set_tabu(va, n1, it + P.tenure);
+          if (is_swap) tb.set_tabu(vb, n2, it + P.tenure);
+        }
+        pva = va;
+        pvb = vb;
+        first_move = false;
         Z = Znew;
         if (improved) {
           zbest = Znew;
