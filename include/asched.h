@@ -542,6 +542,9 @@ int asched_travel_matrix(const asched_travel_spec* spec, int32_t* travel, int32_
  * barrier before and after its work. Per thread the work is iters steps of
  *   ASCHED_PROBE_INT32       ASCHED_PROBE_INT32_OPS_PER_STEP int32 add / xor / min
  *                            operations (8 independent chains);
+ *   ASCHED_PROBE_INT32_ADD_XOR  ASCHED_PROBE_INT32_ADD_XOR_OPS_PER_STEP int32 add / xor
+ *                            operations (8 independent chains; no min, which issues on
+ *                            fewer pipes);
  *   ASCHED_PROBE_LDS         ASCHED_PROBE_LDS_LOADS_PER_STEP 32-bit shared-memory loads,
  *                            the 32 lanes of a warp on 32 distinct banks;
  *   ASCHED_PROBE_LDS_GATHER  as many loads, each lane at a random word of a 64 KB table.
@@ -553,7 +556,9 @@ int asched_travel_matrix(const asched_travel_spec* spec, int32_t* travel, int32_
 #define ASCHED_PROBE_INT32 0
 #define ASCHED_PROBE_LDS 1
 #define ASCHED_PROBE_LDS_GATHER 2
+#define ASCHED_PROBE_INT32_ADD_XOR 3
 #define ASCHED_PROBE_INT32_OPS_PER_STEP 96
+#define ASCHED_PROBE_INT32_ADD_XOR_OPS_PER_STEP 64
 #define ASCHED_PROBE_LDS_LOADS_PER_STEP 16
 int asched_probe_sm_peak(int32_t kind, int32_t iters, int64_t* rec, int32_t rec_ctas, uint32_t* sink,
                          int32_t* ctas_out, int32_t* threads_out, void* stream);

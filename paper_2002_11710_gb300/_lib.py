@@ -113,8 +113,8 @@ SWEEP_ACCEPT_WORSE = 4  # asched_params.flags bits for the sweeps
 SWEEP_REPAIR = 8
 INFO_MOVES, INFO_STEPS = 6, 7
 
-PROBE_INT32, PROBE_LDS, PROBE_LDS_GATHER = 0, 1, 2
-PROBE_INT32_OPS_PER_STEP, PROBE_LDS_LOADS_PER_STEP = 96, 16
+PROBE_INT32, PROBE_LDS, PROBE_LDS_GATHER, PROBE_INT32_ADD_XOR = 0, 1, 2, 3
+PROBE_INT32_OPS_PER_STEP, PROBE_LDS_LOADS_PER_STEP, PROBE_INT32_ADD_XOR_OPS_PER_STEP = 96, 16, 64
 
 
 # Every entry point of include/asched.h with its ctypes signature.

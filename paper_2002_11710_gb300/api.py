@@ -596,8 +596,8 @@ def travel_matrix(coords, speeds_kmh, metric: int = METRIC_EUCLIDEAN, radius_km:
 # --------------------------------------------------------------- roofline probes --
 
 def measure_sm_peaks(device="cuda", iters: int = 4000, repeats: int = 3):
-    """Per-SM rates of the roofline probes (asched_probe_sm_peak): int32 operations,
-    conflict-free shared-memory words and randomly gathered shared-memory words per SM
+    """Per-SM rates of the roofline probes (asched_probe_sm_peak): int32 operations (add /
+    xor / min and add / xor mixes), conflict-free shared-memory words and randomly gathered shared-memory words per SM
     clock, each the median over SMs of (work of the SM's CTAs) / (cycles from the SM's
     first start to its last end), best of `repeats` launches. Also the SM count."""
     dev = torch.device(device)
@@ -605,11 +605,13 @@ def measure_sm_peaks(device="cuda", iters: int = 4000, repeats: int = 3):
     cap = 32 * sms
     rec = torch.zeros(3 * cap, dtype=torch.int64, device=dev)
     sink = torch.zeros(cap, dtype=torch.int32, device=dev)
-    work = {_lib.PROBE_INT32: _lib.PROBE_INT32_OPS_PER_STEP, _lib.PROBE_LDS: _lib.PROBE_LDS_LOADS_PER_STEP,
+    work = {_lib.PROBE_INT32: _lib.PROBE_INT32_OPS_PER_STEP,
+            _lib.PROBE_INT32_ADD_XOR: _lib.PROBE_INT32_ADD_XOR_OPS_PER_STEP,
+            _lib.PROBE_LDS: _lib.PROBE_LDS_LOADS_PER_STEP,
             _lib.PROBE_LDS_GATHER: _lib.PROBE_LDS_LOADS_PER_STEP}
     out = {"sms": sms}
-    names = {_lib.PROBE_INT32: "int32_ops_per_clk_sm", _lib.PROBE_LDS: "lds_words_per_clk_sm",
-             _lib.PROBE_LDS_GATHER: "lds_gather_words_per_clk_sm"}
+    names = {_lib.PROBE_INT32: "int32_ops_per_clk_sm", _lib.PROBE_INT32_ADD_XOR: "int32_add_xor_ops_per_clk_sm",
+             _lib.PROBE_LDS: "lds_words_per_clk_sm", _lib.PROBE_LDS_GATHER: "lds_gather_words_per_clk_sm"}
     s = torch.cuda.current_stream(dev)
     for kind, per_step in work.items():
         best = 0.0

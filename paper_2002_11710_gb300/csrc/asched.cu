@@ -388,6 +388,7 @@ enum { MISC_BAD = 0, MISC_MAXT, MISC_Z0, MISC_GREEDY_FAIL, MISC_CSR_BAD, MISC_ST
 
 struct Ctx {  // per-launch constants every thread keeps in registers
   int M, V, N, L, Mp, cap, horizon, lam;
+  int heli;  // some mission is heli-only
 };
 
 // Table access for either layout. A row handle is (type offset + location) times the
@@ -510,11 +511,13 @@ __device__ __forceinline__ uint8_t move_flags(bool feas, bool tabu, bool asp, bo
 // Relocation R(m, y): take m out, put it immediately before node y. The inputs are
 // already loaded: m's node word, removal delta and RP record, the gap record g of y, the
 // table entries a = A[row of prev(y)][m], b = B[row of y][m], y's vehicle slack fy and
-// the tabu stamp of (m, vehicle of y).
-template <bool PEN, bool DL, bool DEBUG, bool RP>
-__device__ __forceinline__ uint64_t reloc_one(const Smem& sm, const State& S, const Ctx& c, int y, int m,
-                                              int nvm, int rem, int rp, const int4& g, int a, int b, int fy,
-                                              int stamp, int it, int Z, int zbest, const KParams& P) {
+// the tabu stamp of (m, vehicle of y). zrel = z_best - Z, so the move aspires when
+// delta < zrel (Z + delta < z_best). An admissible move's key replaces acc when smaller.
+// HELI: the instance has heli-only missions (else the compatibility test is always true).
+template <bool PEN, bool DL, bool DEBUG, bool RP, bool HELI>
+__device__ __forceinline__ void reloc_one(const Smem& sm, const State& S, const Ctx& c, int y, int m, int nvm,
+                                          int rem, int rp, const int4& g, int a, int b, int fy, int stamp, int it,
+                                          int zrel, const KParams& P, uint64_t& acc) {
   const bool valid = (y != m) && (y != nv_next(nvm));
   const int vm = nv_veh(nvm), vy = nv_veh(g.w);
   const int ins = a + b - g.z;
@@ -545,14 +548,14 @@ __device__ __forceinline__ uint64_t reloc_one(const Smem& sm, const State& S, co
       feas = same ? (fy + d <= 0) : ((fm + rem <= 0) && (fy + ins <= 0));
     }
   }
-  feas = feas && !((nvm >> 24) & (g.w >> 23) & 1);  // heli-only m onto a plane
+  if (HELI) feas = feas && !((nvm >> 24) & (g.w >> 23) & 1);  // heli-only m onto a plane
   if (DL) {
     const int4 dy = S.d4()[y];
     const int w = sm.wm[m];
     feas = feas && (dy.x + a <= w) && (w + b <= dy.y) && S.d4()[m].w;
   }
   const bool tabu = stamp >= it;
-  const bool asp = Z + delta < zbest;
+  const bool asp = delta < zrel;
   const bool adm = valid && feas && (!tabu || asp);
   const uint32_t id = (static_cast<uint32_t>(m) << kIdShift) | static_cast<uint32_t>(y);
   if (DEBUG && valid) {
@@ -561,15 +564,15 @@ __device__ __forceinline__ uint64_t reloc_one(const Smem& sm, const State& S, co
     P.dbg_flags[idx] = move_flags(feas, tabu, asp, adm);
     if (P.dbg_id) P.dbg_id[idx] = id;
   }
-  return adm ? pack_key(delta, id) : kNoKey;
+  const uint64_t k = pack_key(delta, id);
+  if (adm && k < acc) acc = k;
 }
 
 // Relocations of the mission pair (m0, m0 + 1), m0 even, before node y: every load
 // serves both (64-bit loads of consecutive table and record entries).
-template <bool PEN, bool DL, bool DEBUG, bool BIG, bool RP>
-__device__ __forceinline__ uint64_t eval_relocate_pair(const Smem& sm, const Tab<BIG>& tb, const State& S,
-                                                       const Ctx& c, int y, int m0, int it, int Z, int zbest,
-                                                       const KParams& P) {
+template <bool PEN, bool DL, bool DEBUG, bool BIG, bool RP, bool HELI>
+__device__ __forceinline__ void eval_relocate_pair(const Smem& sm, const Tab<BIG>& tb, const State& S, const Ctx& c,
+                                                   int y, int m0, int it, int zrel, const KParams& P, uint64_t& acc) {
   const int4 rr = *reinterpret_cast<const int4*>(S.r2() + m0);  // {nv, rem} of m0 and m0 + 1
   const int2 rp = RP ? *reinterpret_cast<const int2*>(S.rp() + m0) : make_int2(0, 0);
   const int4 g = S.y4()[y];  // A row, B row, leg into y, node word of y
@@ -578,12 +581,10 @@ __device__ __forceinline__ uint64_t eval_relocate_pair(const Smem& sm, const Tab
   const int2 b2 = tb.b2(g.y, m0);
   const int2 st = tb.tabu2(vy, m0);
   const int fy = S.fb()[vy];
-  uint64_t k =
-      reloc_one<PEN, DL, DEBUG, RP>(sm, S, c, y, m0, rr.x, rr.y, rp.x, g, a2.x, b2.x, fy, st.x, it, Z, zbest, P);
+  reloc_one<PEN, DL, DEBUG, RP, HELI>(sm, S, c, y, m0, rr.x, rr.y, rp.x, g, a2.x, b2.x, fy, st.x, it, zrel, P, acc);
   if (m0 + 1 < c.M)
-    k = min_u64(k, reloc_one<PEN, DL, DEBUG, RP>(sm, S, c, y, m0 + 1, rr.z, rr.w, rp.y, g, a2.y, b2.y, fy, st.y, it,
-                                             Z, zbest, P));
-  return k;
+    reloc_one<PEN, DL, DEBUG, RP, HELI>(sm, S, c, y, m0 + 1, rr.z, rr.w, rp.y, g, a2.y, b2.y, fy, st.y, it, zrel, P,
+                                        acc);
 }
 
 // Cost parts of swap S(a, b), each mission taking the other's place: t1 = fly from the
@@ -614,10 +615,10 @@ __device__ __forceinline__ SwapParts swap_parts(const Smem& sm, const Tab<BIG>& 
   return q;
 }
 
-// Swap S(a, b): the two missions exchange places.
-template <bool PEN, bool DL, bool DEBUG, bool BIG>
-__device__ __forceinline__ uint64_t eval_swap(const Smem& sm, const Tab<BIG>& tb, const State& S, const Ctx& c,
-                                              int a, int b, int it, int Z, int zbest, const KParams& P) {
+// Swap S(a, b): the two missions exchange places. Aspiration and the key as in reloc_one.
+template <bool PEN, bool DL, bool DEBUG, bool BIG, bool HELI>
+__device__ __forceinline__ void eval_swap(const Smem& sm, const Tab<BIG>& tb, const State& S, const Ctx& c, int a,
+                                          int b, int it, int zrel, const KParams& P, uint64_t& acc) {
   const SwapParts q = swap_parts<BIG>(sm, tb, S, c, a, b);
   const int nva = q.sa.x, nvb = q.sb.x;
   const int va = nv_veh(nva), vb = nv_veh(nvb);
@@ -636,7 +637,7 @@ __device__ __forceinline__ uint64_t eval_swap(const Smem& sm, const Tab<BIG>& tb
     delta = d;
     feas = same ? (fa + d <= 0) : ((fa + da <= 0) && (fb + db <= 0));
   }
-  feas = feas && !((((nva >> 24) & (nvb >> 23)) | ((nvb >> 24) & (nva >> 23))) & 1);
+  if (HELI) feas = feas && !((((nva >> 24) & (nvb >> 23)) | ((nvb >> 24) & (nva >> 23))) & 1);
   if (DL) {
     const int4 xa = S.d4()[a], xb = S.d4()[b];
     const int wa = sm.wm[a], wb = sm.wm[b];
@@ -647,7 +648,7 @@ __device__ __forceinline__ uint64_t eval_swap(const Smem& sm, const Tab<BIG>& tb
     feas = feas && l1 && l2 && l3 && l4;
   }
   const bool tabu = (tb.tabu(vb, a) >= it) || (tb.tabu(va, b) >= it);
-  const bool asp = Z + delta < zbest;
+  const bool asp = delta < zrel;
   const bool adm = feas && (!tabu || asp);
   const int m1 = a < b ? a : b, m2 = a < b ? b : a;
   const uint32_t id = kSwapBit | (static_cast<uint32_t>(m1) << kIdShift) | static_cast<uint32_t>(m2);
@@ -658,7 +659,42 @@ __device__ __forceinline__ uint64_t eval_swap(const Smem& sm, const Tab<BIG>& tb
     P.dbg_flags[idx] = move_flags(feas, tabu, asp, adm);
     if (P.dbg_id) P.dbg_id[idx] = id;
   }
-  return adm ? pack_key(delta, id) : kNoKey;
+  const uint64_t k = pack_key(delta, id);
+  if (adm && k < acc) acc = k;
+}
+
+// One thread's share of the evaluation (see the main loop for the item list and how its
+// coordinates advance); returns the least admissible key among its moves.
+struct ItemCursor {
+  int r_y, r_h, s_j, s_row, s_a;  // first relocation item (y, h) and swap item (j, row, a)
+  int Gq, Gr, Sq, Sr, G, H, Sn;   // grid stride in both coordinate systems, list sizes
+};
+
+template <bool PEN, bool DL, bool DEBUG, bool BIG, bool RP, bool HELI>
+__device__ __forceinline__ uint64_t eval_items(const Smem& sm, const Tab<BIG>& tb, const State& S, const Ctx& c,
+                                               const ItemCursor& q, int it, int zrel, const KParams& P) {
+  uint64_t key = kNoKey;
+  for (int y = q.r_y, h = q.r_h; y < c.N;) {
+    eval_relocate_pair<PEN, DL, DEBUG, BIG, RP, HELI>(sm, tb, S, c, y, 2 * h, it, zrel, P, key);
+    h += q.Gr;
+    y += q.Gq;
+    if (h >= q.H) {
+      h -= q.H;
+      ++y;
+    }
+  }
+  for (int j = q.s_j, row = q.s_row, a = q.s_a; j < q.Sn; j += q.G) {
+    int b = a + row + 1;
+    if (b >= c.M) b -= c.M;
+    eval_swap<PEN, DL, DEBUG, BIG, HELI>(sm, tb, S, c, a, b, it, zrel, P, key);
+    a += q.Sr;
+    row += q.Sq;
+    if (a >= c.M) {
+      a -= c.M;
+      ++row;
+    }
+  }
+  return key;
 }
 
 // Flight after move `id` of the source route (src) or of the target route (!src): the
@@ -809,12 +845,13 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
   // ---- prologue 1: static per-mission / per-node data and validation
   if (tid < 16) sm.misc[tid] = 0;
   __syncthreads();
-  int bad = 0;
+  int bad = 0, any_heli = 0;
   for (int i = tid; i < Mp; i += nthr) {
     if (i < M) {
       const int p = gin(P.pickup + i), d = gin(P.delivery + i);
       const int h = P.heli_only ? gin(P.heli_only + i) : 0;
       bad |= (p < 0) | (p >= L) | (d < 0) | (d >= L) | (p == d) | (h < 0) | (h > 1);
+      any_heli |= h != 0;
       sm.wm[i] = P.deadline ? gin(P.deadline + i) : 0;
       sm.eloc[i] = d;
       sm.sloc[i] = p;
@@ -842,6 +879,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
     }
   }
   if (__syncthreads_or(bad)) status = ASCHED_E_INVALID;
+  c.heli = __syncthreads_or(any_heli);
   if (BIG && status == ASCHED_OK) {
     // ---- prologue 1b: the int16 matrix, staged through shared memory by bulk copies,
     // checked as it is converted
@@ -1099,32 +1137,18 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
         s_a = s_j - s_row * M;
       }
     }
+    const ItemCursor cursor{r_y, r_h, s_j, s_row, s_a, Gq, Gr, Sq, Sr, G, H, Sn};
     const int iters = DEBUG ? 1 : P.iterations;
     for (it = 0; it < iters; ++it) {
       const State S = sm.st(cur);
       const int it_eval = DEBUG ? P.dbg_it : it;
       const int zb_eval = DEBUG ? P.dbg_zbest : zbest;
-      uint64_t key = kNoKey;
-      for (int y = r_y, h = r_h; y < N;) {
-        key = min_u64(key, eval_relocate_pair<PEN, DL, DEBUG, BIG, RP>(sm, tb, S, c, y, 2 * h, it_eval, Z, zb_eval, P));
-        h += Gr;
-        y += Gq;
-        if (h >= H) {
-          h -= H;
-          ++y;
-        }
-      }
-      for (int j = s_j, row = s_row, a = s_a; j < Sn; j += G) {
-        int b = a + row + 1;
-        if (b >= M) b -= M;
-        key = min_u64(key, eval_swap<PEN, DL, DEBUG, BIG>(sm, tb, S, c, a, b, it_eval, Z, zb_eval, P));
-        a += Sr;
-        row += Sq;
-        if (a >= M) {
-          a -= M;
-          ++row;
-        }
-      }
+      // z_best - Z, clamped to int32 (a caller's z_best is arbitrary in DEBUG mode; every
+      // delta lies well inside the int32 range, so the clamp changes no comparison)
+      const int64_t zr = static_cast<int64_t>(zb_eval) - Z;
+      const int zrel = static_cast<int>(zr < INT32_MIN ? INT32_MIN : (zr > INT32_MAX ? INT32_MAX : zr));
+      uint64_t key = c.heli ? eval_items<PEN, DL, DEBUG, BIG, RP, true>(sm, tb, S, c, cursor, it_eval, zrel, P)
+                            : eval_items<PEN, DL, DEBUG, BIG, RP, false>(sm, tb, S, c, cursor, it_eval, zrel, P);
       key = warp_min_key(key);
       if (lane == 0) sm.warpkey()[warp] = key;
       __syncthreads();

@@ -9,6 +9,7 @@
 // the last end). Work is counted in the units the roofline uses:
 //   ASCHED_PROBE_INT32        int32 operations (add, xor, min; 8 independent chains per
 //                             thread, so issue and not latency bounds it);
+//   ASCHED_PROBE_INT32_ADD_XOR the same without the min;
 //   ASCHED_PROBE_LDS          32-bit shared-memory words loaded, conflict-free (the 32
 //                             lanes of a warp read 32 distinct banks);
 //   ASCHED_PROBE_LDS_GATHER   the same with every lane at a random word of a 64 KB table
@@ -25,6 +26,7 @@ constexpr int kUnroll = 4;
 constexpr int kTabWords = 16384;  // 64 KB table for the load probes
 constexpr int kLoadsPerStep = ASCHED_PROBE_LDS_LOADS_PER_STEP;
 static_assert(kChains * kUnroll * 3 == ASCHED_PROBE_INT32_OPS_PER_STEP, "ops per step");
+static_assert(kChains * kUnroll * 2 == ASCHED_PROBE_INT32_ADD_XOR_OPS_PER_STEP, "ops per step");
 static_assert(kTabWords / 2 + 32 * kLoadsPerStep <= kTabWords, "loads stay inside the table");
 
 __device__ __forceinline__ uint32_t sm_id() {
@@ -41,6 +43,9 @@ __device__ __forceinline__ void record(int64_t* rec, long long t0, long long t1)
   }
 }
 
+// MIN: add / xor / min per chain and step; otherwise add / xor (no reassociation can
+// merge the steps of a chain: every add is followed by an xor).
+template <bool MIN>
 __global__ void probe_int32_kernel(int iters, uint32_t c, uint32_t d, uint32_t e, int64_t* rec, uint32_t* sink) {
   uint32_t a[kChains];
 #pragma unroll
@@ -54,7 +59,7 @@ __global__ void probe_int32_kernel(int iters, uint32_t c, uint32_t d, uint32_t e
       for (int k = 0; k < kChains; ++k) {
         asm("add.u32 %0, %0, %1;" : "+r"(a[k]) : "r"(c));
         asm("xor.b32 %0, %0, %1;" : "+r"(a[k]) : "r"(d));
-        asm("min.u32 %0, %0, %1;" : "+r"(a[k]) : "r"(e));
+        if (MIN) asm("min.u32 %0, %0, %1;" : "+r"(a[k]) : "r"(e));
       }
     }
   }
@@ -129,10 +134,12 @@ extern "C" int asched_probe_sm_peak(int32_t kind, int32_t iters, int64_t* rec, i
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int threads = 512;
   *threads_out = threads;
-  if (kind == ASCHED_PROBE_INT32) {
+  if (kind == ASCHED_PROBE_INT32 || kind == ASCHED_PROBE_INT32_ADD_XOR) {
     uint32_t c = 0x9E37u, d = 0x5bd1e995u, e = 0xFFFFFF00u;
     void* args[] = {&iters, &c, &d, &e, &rec, &sink};
-    return launch_probe(reinterpret_cast<void*>(&probe_int32_kernel), threads, 0, args, rec, rec_ctas, ctas_out, st);
+    void* fn = kind == ASCHED_PROBE_INT32 ? reinterpret_cast<void*>(&probe_int32_kernel<true>)
+                                          : reinterpret_cast<void*>(&probe_int32_kernel<false>);
+    return launch_probe(fn, threads, 0, args, rec, rec_ctas, ctas_out, st);
   }
   if (kind == ASCHED_PROBE_LDS || kind == ASCHED_PROBE_LDS_GATHER) {
     void* args[] = {&iters, &rec, &sink};

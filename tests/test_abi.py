@@ -125,3 +125,19 @@ def test_validate_and_workspace_entry_points_host_paths():
     assert L.asched_workspace_bytes(ctypes.byref(s), ctypes.byref(_params(cap_mode=9)),
                                     ctypes.byref(n)) == api.E_INVALID
     assert L.asched_workspace_bytes(ctypes.byref(s), ctypes.byref(_params()), None) == api.E_INVALID
+
+
+def test_binding_constants_match_the_header():
+    """Every integer #define ASCHED_<NAME> of include/asched.h that the binding mirrors
+    (as _lib.<NAME>) has the same value there (status codes in parentheses included)."""
+    import re
+
+    from paper_2002_11710_gb300 import _lib
+
+    text = open(os.path.join(ROOT, "include", "asched.h")).read()
+    checked = 0
+    for name, val in re.findall(r"#define ASCHED_([A-Z0-9_]+)\s+\(?(-?(?:0x[0-9A-Fa-f]+|\d+))u?\)?", text):
+        if hasattr(_lib, name):
+            assert getattr(_lib, name) == int(val, 0), name
+            checked += 1
+    assert checked >= 40
