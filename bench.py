@@ -441,6 +441,11 @@ def run_gpu(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def _shape_name(c):
+    """'threads[/int16][/xC]' for an autotune candidate (threads, compact, CTAs per instance)."""
+    return f"{c[0]}{'/int16' if c[1] else ''}{f'/x{c[2]}' if c[2] > 1 else ''}"
+
+
 def run_batched(args, dev, rank, world):
     """The batched workload: 1,024 instances (V ~ U[3, 30], M ~ U[10, 200], paper-shaped
     geography, 2,000 iterations each) in one persistent launch replayed from a CUDA graph,
@@ -457,7 +462,8 @@ def run_batched(args, dev, rank, world):
     bp = api.BatchProblem(insts, dev)
     choice, tune = api.autotune_batch(bp, api.params_from(p))
     params = api.tuned_params(api.params_from(p), choice)
-    thr = {"block_threads": choice[0], "layout": "int16 matrix" if choice[1] else "gather tables"}
+    thr = {"block_threads": choice[0], "layout": "int16 matrix" if choice[1] else "gather tables",
+           "ctas_per_instance": choice[2], "moves_per_warp": api.batch_moves_per_warp(bp, choice)}
     graph, out = api.capture_batch(bp, params)
     for _ in range(max(1, args.warmup // 2)):
         graph.replay()
@@ -490,7 +496,9 @@ def run_batched(args, dev, rank, world):
     return {"workload": "1,024 instances, V ~ U[3,30], M ~ U[10,200], 2,000 iterations each, "
                         "replayed from a captured CUDA graph",
             "ms": t, "solves_per_s": 1024 / t * 1e3, "moves_per_s": moves / t * 1e3,
-            "launch_shape": thr, "autotune_ms": {f"{t}{'/int16' if c else ''}": v for (t, c), v in tune.items()},
+            "launch_shape": thr,
+            "autotune_ms": {_shape_name(c): v for c, v in tune.items()},
+            "autotune_moves_per_warp": {_shape_name(c): api.batch_moves_per_warp(bp, c) for c in tune},
             "instances_ok": ok, "shard": f"contiguous block of {hi - lo} instances per rank ({world} ranks)",
             "sequential_ms": seq_ms, "sequential_solves_per_s": 1024 / seq_ms * 1e3,
             "speedup_vs_sequential": seq_ms / t, "gpu_launches": 2}

@@ -274,8 +274,10 @@ int asched_eval_neighbourhood(const asched_instance* inst, const asched_params* 
                               unsigned long long* best_key_out, int32_t* info, void* stream);
 
 /* ---------------------------------------------------------------- batches ----------
- * Many independent instances solved by one persistent launch (one CTA per instance
- * at a time, instances taken largest first from a device work queue). The arrays of
+ * Many independent instances solved by one persistent launch (instances taken largest
+ * first from a device work queue; each solved by one CTA, or with cluster_size C in
+ * {2, 4, 8, 16} by a thread-block cluster of C CTAs, as many clusters as the device
+ * holds at once; results do not depend on C). The arrays of
  * all instances are concatenated; instance b owns
  *   locations  [loc_off[b], loc_off[b+1]),  L_b = loc_off[b+1] - loc_off[b]
  *   vehicles   [veh_off[b], veh_off[b+1]),  V_b >= 1
@@ -284,7 +286,7 @@ int asched_eval_neighbourhood(const asched_instance* inst, const asched_params* 
  * Location indices (veh_base, pickup, delivery) are local to the instance. The three
  * offset arrays are given twice: h_* in host memory (read by the call to size the
  * launch) and as device copies (read by the kernel); they must agree.
- * Every instance shares the asched_params (cluster_size must be 0 or 1). */
+ * Every instance shares the asched_params (cluster_size 0 means 1 here). */
 typedef struct {
   int32_t n_instances;
   int32_t n_types;

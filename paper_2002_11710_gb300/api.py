@@ -411,23 +411,54 @@ def solve_batch(bp: BatchProblem, params: _lib.Params, out: Optional[BatchOutput
     return out
 
 
-def autotune_batch(bp: BatchProblem, params: _lib.Params,
-                   candidates=((512, False), (384, False), (256, False), (256, True), (128, True)),
+BATCH_CANDIDATES = ((512, False, 1), (384, False, 1), (256, False, 1), (256, True, 1), (128, True, 1),
+                    (512, False, 2), (256, False, 2), (512, False, 4))
+
+
+def _shape(cand):
+    """(block threads, compact, CTAs per instance) of an autotune candidate given as a
+    block size, a (threads, compact) pair or a full triple."""
+    if isinstance(cand, int):
+        return int(cand), False, 1
+    if len(cand) == 2:
+        return int(cand[0]), bool(cand[1]), 1
+    return int(cand[0]), bool(cand[1]), int(cand[2])
+
+
+def batch_moves_per_warp(bp: "BatchProblem", cand) -> float:
+    """Moves each warp evaluates per iteration, averaged over the batch's instances, for
+    an autotune candidate: the neighbourhood over the warps of the CTAs that solve one
+    instance (the moves-per-warp axis the block size and CTAs per instance set)."""
+    thr, _, cl = _shape(cand)
+    moves = [num_moves(int(m), int(v)) for m, v in zip(np.diff(bp.h_mis_off), np.diff(bp.h_veh_off))]
+    return float(np.mean(moves)) / (thr // 32 * cl) if moves else 0.0
+
+
+def autotune_batch(bp: BatchProblem, params: _lib.Params, candidates=BATCH_CANDIDATES,
                    probe_iterations: int = 200, repeats: int = 2):
     """Pick the launch shape of a batch by timing short probe runs of each candidate
-    (CUDA events on the current stream): (block threads, compact) pairs, compact meaning
-    the int16 matrix layout for every instance (smaller state, more resident CTAs) instead
-    of the gather tables where they fit; a plain int is a block size with the tables.
+    (CUDA events on the current stream). A candidate is (block threads, compact, CTAs per
+    instance): compact means the int16 matrix layout for every instance (smaller state,
+    more resident CTAs) instead of the gather tables where they fit; CTAs per instance > 1
+    solves each instance by a thread-block cluster of that many CTAs. Block size and CTAs
+    per instance together set the moves each warp evaluates (batch_moves_per_warp). A
+    plain int is a block size, a pair (threads, compact) has one CTA per instance.
     Results never depend on the choice; only the time does. Returns (best candidate,
-    {candidate: ms}) with candidates as (threads, compact) pairs."""
+    {candidate: ms}) with candidates as triples; shapes the device cannot launch (a
+    cluster that does not fit) are left out."""
     out = bp.alloc_output()
     times = {}
     for cand in candidates:
-        thr, compact = (cand, False) if isinstance(cand, int) else (int(cand[0]), bool(cand[1]))
+        thr, compact, cl = _shape(cand)
         probe = _lib.Params(params.tenure, min(params.iterations, probe_iterations), params.cap_mode,
-                            params.lam, params.cluster_size, thr, params.timeout_ns,
+                            params.lam, cl, thr, params.timeout_ns,
                             (params.flags & ~COMPACT_LAYOUT) | (COMPACT_LAYOUT if compact else 0))
-        solve_batch(bp, probe, out=out)  # warm-up
+        try:
+            solve_batch(bp, probe, out=out)  # warm-up
+        except _lib.AschedError as e:
+            if e.status == E_TOO_LARGE and cl > 1:
+                continue
+            raise
         best = None
         for _ in range(repeats):
             a = torch.cuda.Event(enable_timing=True)
@@ -438,14 +469,14 @@ def autotune_batch(bp: BatchProblem, params: _lib.Params,
             b.synchronize()
             ms = a.elapsed_time(b)
             best = ms if best is None else min(best, ms)
-        times[(thr, compact)] = best
+        times[(thr, compact, cl)] = best
     return min(times, key=times.get), times
 
 
 def tuned_params(params: _lib.Params, choice) -> _lib.Params:
     """params with the launch shape an autotune_batch choice names."""
-    thr, compact = choice
-    return _lib.Params(params.tenure, params.iterations, params.cap_mode, params.lam, params.cluster_size,
+    thr, compact, cl = _shape(choice)
+    return _lib.Params(params.tenure, params.iterations, params.cap_mode, params.lam, cl,
                        int(thr), params.timeout_ns,
                        (params.flags & ~COMPACT_LAYOUT) | (COMPACT_LAYOUT if compact else 0))
 

@@ -1507,14 +1507,33 @@ __global__ void batch_order_kernel(int32_t B, const int32_t* veh_off, const int3
   if (blockIdx.x == 0 && threadIdx.x == 0) work[0] = 0;
 }
 
-template <bool PEN, bool DL>
+// CL: the launch is made of thread-block clusters of Q.run.cluster CTAs and each instance
+// is solved by a whole cluster (the same search as asched_solve with that cluster size):
+// rank 0 takes the ticket and the other CTAs read it from rank 0's shared memory between
+// two cluster barriers.
+template <bool PEN, bool DL, bool CL>
 __global__ void __launch_bounds__(kMaxThreads, 1) tabu_batch_kernel(const __grid_constant__ BParams Q) {
   __shared__ int s_ticket;
+  const int C = CL ? Q.run.cluster : 1;
+  if (CL && !launch_shape_ok(C, 0)) {  // uniform over the launch: nothing is solved
+    if (blockIdx.x == 0)
+      for (int b = threadIdx.x; b < Q.B; b += blockDim.x)
+        Q.info[static_cast<int64_t>(b) * ASCHED_INFO_LEN + ASCHED_INFO_STATUS] = ASCHED_E_INVALID;
+    return;
+  }
+  const int rank = CL ? static_cast<int>(cluster_rank()) : 0;
   while (true) {
-    if (threadIdx.x == 0) s_ticket = atomicAdd(&Q.work[0], 1);
-    __syncthreads();
-    const int k = s_ticket;
-    __syncthreads();
+    if (rank == 0 && threadIdx.x == 0) s_ticket = atomicAdd(&Q.work[0], 1);
+    int k;
+    if (CL) {
+      cluster_sync_unaligned();  // thread 0 of rank 0 arrives from its claim
+      k = rank == 0 ? s_ticket : ld_peer_i32(mapa_rank(smem_u32(&s_ticket), 0));
+      cluster_sync_unaligned();  // every CTA has read it before rank 0 takes the next
+    } else {
+      __syncthreads();
+      k = s_ticket;
+      __syncthreads();
+    }
     if (k >= Q.B) break;
     const int b = Q.work[1 + k];
     KParams P = Q.run;
@@ -1540,10 +1559,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) tabu_batch_kernel(const __grid
     // memory, the int16 matrix otherwise.
     const Layout small = make_layout(P.M, P.V, P.L, P.nt, false, true);
     if (!Q.compact && small.total <= Q.smem_words) {
-      solve_one<PEN, DL, false, false, true>(P, small, 1, 0, 1, 0);
+      solve_one<PEN, DL, false, false, true>(P, small, C, rank, 1, 0);
     } else {
       const Layout big = make_layout(P.M, P.V, P.L, P.nt, true, true);
-      solve_one<PEN, DL, false, true, true>(P, big, 1, 0, 1, 0);
+      solve_one<PEN, DL, false, true, true>(P, big, C, rank, 1, 0);
     }
     __syncthreads();  // the next instance's prologue reuses shared memory
   }
@@ -1946,9 +1965,15 @@ int launch(const asched_instance* inst, const asched_params* p, bool debug, KPar
   return ASCHED_OK;
 }
 
-template <bool PEN, bool DL>
+template <bool PEN, bool DL, bool CL>
 void* batch_kernel_ptr() {
-  return reinterpret_cast<void*>(&tabu_batch_kernel<PEN, DL>);
+  return reinterpret_cast<void*>(&tabu_batch_kernel<PEN, DL, CL>);
+}
+
+template <bool CL>
+void* pick_batch_kernel(bool pen, bool dl) {
+  return pen ? (dl ? batch_kernel_ptr<true, true, CL>() : batch_kernel_ptr<true, false, CL>())
+             : (dl ? batch_kernel_ptr<false, true, CL>() : batch_kernel_ptr<false, false, CL>());
 }
 
 int launch_batch(const asched_batch* bt, const asched_params* p, const asched_batch_result* out,
@@ -1963,7 +1988,6 @@ int launch_batch(const asched_batch* bt, const asched_params* p, const asched_ba
     return ASCHED_E_INVALID;
   if (!out->route_off || !out->route || !out->info || !workspace) return ASCHED_E_INVALID;
   if (ws_bytes < sizeof(int32_t) * (static_cast<size_t>(B) + 1)) return ASCHED_E_INVALID;
-  if (p->cluster_size > 1) return ASCHED_E_INVALID;  // one CTA per instance in a batch
   const int limit = max_smem_optin();
   if (limit < 0) return ASCHED_E_CUDA;
   int max_words = 0;
@@ -1985,28 +2009,38 @@ int launch_batch(const asched_batch* bt, const asched_params* p, const asched_ba
   const int64_t bytes = static_cast<int64_t>(max_words) * 4;
   const bool pen = p->cap_mode == ASCHED_PENALTY;
   const bool dl = bt->deadline != nullptr;
-  void* fn = pen ? (dl ? batch_kernel_ptr<true, true>() : batch_kernel_ptr<true, false>())
-                 : (dl ? batch_kernel_ptr<false, true>() : batch_kernel_ptr<false, false>());
+  // CTAs per instance: 1 (one persistent CTA per SM slot) or a cluster of C CTAs
+  const int C = p->cluster_size > 1 ? p->cluster_size : 1;
+  void* fn = C > 1 ? pick_batch_kernel<true>(pen, dl) : pick_batch_kernel<false>(pen, dl);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)) !=
       cudaSuccess)
     return ASCHED_E_CUDA;
   const int threads = p->block_threads ? p->block_threads : kMaxThreads;
-  int dev = 0, sms = 0, per_sm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, static_cast<size_t>(bytes)) !=
-          cudaSuccess) {
-    (void)cudaGetLastError();
-    return ASCHED_E_CUDA;
+  int grid = 0;
+  if (C > 1) {
+    int n = 0;
+    const int rc = active_clusters(fn, C, threads, static_cast<int>(bytes), &n);
+    if (rc != ASCHED_OK) return rc;
+    if (n < 1) return ASCHED_E_TOO_LARGE;
+    grid = (B < n ? B : n) * C;
+  } else {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, static_cast<size_t>(bytes)) !=
+            cudaSuccess) {
+      (void)cudaGetLastError();
+      return ASCHED_E_CUDA;
+    }
+    if (per_sm < 1) return ASCHED_E_TOO_LARGE;
+    grid = B < sms * per_sm ? B : sms * per_sm;
   }
-  if (per_sm < 1) return ASCHED_E_TOO_LARGE;
-  const int grid = B < sms * per_sm ? B : sms * per_sm;
   BParams q = {};
   q.run.nt = bt->n_types;
   q.run.tenure = p->tenure;
   q.run.iterations = p->iterations;
   q.run.lambda = pen ? p->lambda : 0;
-  q.run.cluster = 1;
+  q.run.cluster = C;
   q.run.timeout_ns = p->timeout_ns > 0 ? p->timeout_ns : kDefaultTimeoutNs;
   q.B = B;
   q.smem_words = max_words;
@@ -2034,7 +2068,19 @@ int launch_batch(const asched_batch* bt, const asched_params* p, const asched_ba
   batch_order_kernel<<<(B + 255) / 256, 256, 0, st>>>(B, bt->veh_off, bt->mis_off, q.work);
   if (cudaGetLastError() != cudaSuccess) return ASCHED_E_CUDA;
   void* args[] = {&q};
-  if (cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, static_cast<size_t>(bytes), st) != cudaSuccess) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = static_cast<size_t>(bytes);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = C > 1 ? 1 : 0;
+  if (cudaLaunchKernelExC(&cfg, fn, args) != cudaSuccess) {
     (void)cudaGetLastError();
     return ASCHED_E_CUDA;
   }

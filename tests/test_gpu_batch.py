@@ -157,7 +157,7 @@ def test_batch_host_errors():
     insts = _mixed_instances()[:3]
     bp = api.BatchProblem(insts)
     with pytest.raises(api.AschedError) as e:
-        api.solve_batch(bp, api.make_params(3, 5, PENALTY, 1000, cluster_size=2))
+        api.solve_batch(bp, api.make_params(3, 5, PENALTY, 1000, cluster_size=3))
     assert e.value.status == api.E_INVALID
     huge = gen.random_instance(9, n_loc=300, n_vehicles=60, n_missions=900, n_types=2,
                                duty_cap=100000)
@@ -178,9 +178,12 @@ def test_batch_independent_of_block_size_and_autotuner_picks_a_candidate():
     for o in outs[1:]:
         for b in range(len(insts)):
             _same(bp.unpack(outs[0], b), bp.unpack(o, b))
-    best, times = api.autotune_batch(bp, api.make_params(4, 30, PENALTY, 1000),
-                                     candidates=((256, False), (128, True)), probe_iterations=10, repeats=1)
-    assert best in ((256, False), (128, True)) and set(times) == {(256, False), (128, True)}
+    cands = ((256, False), (128, True), (256, False, 2))
+    best, times = api.autotune_batch(bp, api.make_params(4, 30, PENALTY, 1000), candidates=cands,
+                                     probe_iterations=10, repeats=1)
+    assert best in times and set(times) == {(256, False, 1), (128, True, 1), (256, False, 2)}
+    assert api.batch_moves_per_warp(bp, (256, False, 2)) * 2 == pytest.approx(
+        api.batch_moves_per_warp(bp, (256, False, 1)))
     tuned = api.tuned_params(api.make_params(4, 30, PENALTY, 1000), best)
     got = api.solve_batch(bp, tuned)
     torch.cuda.synchronize()
@@ -202,3 +205,18 @@ def test_batch_replayed_from_a_cuda_graph_matches_direct_calls():
         torch.cuda.synchronize()
         for b in range(len(insts)):
             _same(bp.unpack(out, b), bp.unpack(direct, b))
+
+
+@pytest.mark.parametrize("cluster", [2, 4, 16])
+def test_batch_solved_by_clusters_equals_one_cta_per_instance(cluster):
+    """CTAs per instance (a thread-block cluster solving each instance) changes nothing in
+    the results: every member equals the one-CTA batch, which equals single solves."""
+    insts = _mixed_instances()
+    params = api.make_params(5, 40, PENALTY, 1000)
+    bp = api.BatchProblem(insts)
+    ref = api.solve_batch(bp, params)
+    got = api.solve_batch(bp, api.make_params(5, 40, PENALTY, 1000, cluster_size=cluster, block_threads=128))
+    torch.cuda.synchronize()
+    for b in range(len(insts)):
+        _same(bp.unpack(ref, b), bp.unpack(got, b))
+    _same(bp.unpack(got, 0), _single(insts[0], params))
