@@ -412,12 +412,25 @@ struct Tab {
     }
     return g_smem[B + r + m];
   }
-  __device__ __forceinline__ int2 a2(int r, int m0) const {  // m0 even
-    if (BIG) return make_int2(a(r, m0), a(r, m0 + 1));
+  // Entries of missions m0 and m0 + 1 (m0 even). The per-mission arrays start on 16-byte
+  // boundaries (every layout offset is a multiple of 4 words), so the pair's locations
+  // and legs come in single 64-bit loads.
+  __device__ __forceinline__ int2 a2(int r, int m0) const {
+    if (BIG) {
+      const int2 s = *reinterpret_cast<const int2*>(g_smem + sloc + m0);
+      const int2 cm = *reinterpret_cast<const int2*>(g_smem + cmat + (r >= L ? Mp : 0) + m0);
+      const int base = r * Ls;
+      return make_int2(t16(base + s.x) + cm.x, t16(base + s.y) + cm.y);
+    }
     return *reinterpret_cast<const int2*>(g_smem + A + r + m0);
   }
   __device__ __forceinline__ int2 b2(int r, int m0) const {
-    if (BIG) return make_int2(b(r, m0), b(r, m0 + 1));
+    if (BIG) {
+      const int tyl = r >= L ? L : 0;
+      const int2 e = *reinterpret_cast<const int2*>(g_smem + eloc + m0);
+      const int col = r - tyl;
+      return make_int2(t16((tyl + e.x) * Ls + col), t16((tyl + e.y) * Ls + col));
+    }
     return *reinterpret_cast<const int2*>(g_smem + B + r + m0);
   }
   __device__ __forceinline__ int tabu(int v, int m) const {
@@ -467,13 +480,14 @@ __device__ __forceinline__ int vw_move(int from, int own) { return (from & 0x7FF
 template <bool PEN, bool DL, bool BIG, bool RP>
 __device__ __forceinline__ void write_records(const Smem& sm, const Tab<BIG>& tb, const State& S2, const Ctx& c,
                                               int t, int nx, int pv, int vw, int f2) {
+  // Every load comes before the first store: the stores go to the same shared array, so
+  // the compiler could not move a load above one of them.
   const int plane = vw_plane(vw);
   const int tyl = plane * c.L, tym = plane * c.Mp;
   const int rowA = tb.row(tyl, sm.eloc[pv]);
   const int rowB = tb.row(tyl, sm.sloc[t]);
   const int nv = nx | (vw << 13);
   const int dep = (DL && pv < c.M) ? sm.wm[pv] : 0;
-  S2.prv()[t] = pv;
   if (t < c.M) {
     const int rowBn = tb.row(tyl, sm.sloc[nx]);
     const int aT = tb.a(rowA, t);
@@ -482,7 +496,10 @@ __device__ __forceinline__ void write_records(const Smem& sm, const Tab<BIG>& tb
     const int ct = sm.cmat[tym + t];
     const int cn = nx < c.M ? sm.cmat[tym + nx] : 0;
     const int leg = nx < c.M ? tb.a(rowA, nx) - cn : (pv < c.M ? tb.b(rowBn, pv) : 0);
+    const int wt = DL ? sm.wm[t] : 0;
+    const int wn = DL ? (nx < c.M ? sm.wm[nx] : c.horizon) : 0;
     const int rem = leg - slot;
+    S2.prv()[t] = pv;
     S2.r2()[t] = make_int2(nv, rem);
     if (RP) {
       const int fm = f2 - c.cap;
@@ -490,12 +507,10 @@ __device__ __forceinline__ void write_records(const Smem& sm, const Tab<BIG>& tb
     }
     S2.y4()[t] = make_int4(rowA, rowB, aT - ct, nv);
     S2.s4()[t] = make_int4(nv, rowA, rowBn, slot);
-    if (DL) {
-      const int wn = nx < c.M ? sm.wm[nx] : c.horizon;
-      S2.d4()[t] = make_int4(dep, sm.wm[t] - ct, wn - cn, (dep + leg + cn <= wn) ? 1 : 0);
-    }
+    if (DL) S2.d4()[t] = make_int4(dep, wt - ct, wn - cn, (dep + leg + cn <= wn) ? 1 : 0);
   } else {
     const int inleg = (pv == t) ? 0 : tb.b(rowB, pv);
+    S2.prv()[t] = pv;
     S2.r2()[t] = make_int2(nv, 0);
     S2.y4()[t] = make_int4(rowA, rowB, inleg, nv);
     S2.s4()[t] = make_int4(nv, 0, 0, 0);
@@ -726,13 +741,21 @@ __device__ __forceinline__ int moved_flight(const Smem& sm, const Tab<BIG>& tb, 
 // Copy every record of node t from buffer S to buffer S2 (t's route is unchanged).
 template <bool DL, bool RP>
 __device__ __forceinline__ void copy_records(const State& S, const State& S2, const Ctx& c, int t) {
-  S2.r2()[t] = S.r2()[t];
-  S2.y4()[t] = S.y4()[t];
-  S2.s4()[t] = S.s4()[t];
-  if (DL) S2.d4()[t] = S.d4()[t];
-  S2.prv()[t] = S.prv()[t];
-  if (t >= c.M) S2.fb()[t - c.M] = S.fb()[t - c.M];
-  if (RP && t < c.M) S2.rp()[t] = S.rp()[t];
+  // all loads first (the stores could alias them as far as the compiler knows)
+  const int2 r2 = S.r2()[t];
+  const int4 y4 = S.y4()[t];
+  const int4 s4 = S.s4()[t];
+  const int4 d4 = DL ? S.d4()[t] : make_int4(0, 0, 0, 0);
+  const int pv = S.prv()[t];
+  const bool end = t >= c.M;
+  const int extra = end ? S.fb()[t - c.M] : (RP ? S.rp()[t] : 0);
+  S2.r2()[t] = r2;
+  S2.y4()[t] = y4;
+  S2.s4()[t] = s4;
+  if (DL) S2.d4()[t] = d4;
+  S2.prv()[t] = pv;
+  if (end) S2.fb()[t - c.M] = extra;
+  else if (RP) S2.rp()[t] = extra;
 }
 
 // ------------------------------------------------------------------ the kernel -----
