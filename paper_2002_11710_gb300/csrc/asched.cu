@@ -631,10 +631,28 @@ __device__ __forceinline__ SwapParts swap_parts(const Smem& sm, const Tab<BIG>& 
 }
 
 // Swap S(a, b): the two missions exchange places. Aspiration and the key as in reloc_one.
-template <bool PEN, bool DL, bool DEBUG, bool BIG, bool HELI>
+// FAR: the main pass over every pair of the batch and serving kernels, which takes the
+// cost parts of two missions that are not neighbours (no delivery rows, no selects) and
+// leaves neighbouring pairs out; those are the pairs (t, next t) of their neighbour pass.
+// FAR = false handles any pair whole (the single-instance kernel's pass over every pair,
+// and the neighbour pass).
+template <bool PEN, bool DL, bool DEBUG, bool BIG, bool HELI, bool FAR>
 __device__ __forceinline__ void eval_swap(const Smem& sm, const Tab<BIG>& tb, const State& S, const Ctx& c, int a,
                                           int b, int it, int zrel, const KParams& P, uint64_t& acc) {
-  const SwapParts q = swap_parts<BIG>(sm, tb, S, c, a, b);
+  SwapParts q;
+  bool near = false;
+  if (FAR) {
+    q.sa = S.s4()[a];
+    q.sb = S.s4()[b];
+    near = nv_next(q.sa.x) == b || nv_next(q.sb.x) == a;
+    q.adjA = q.adjB = false;
+    q.t1 = tb.a(q.sa.y, b);
+    q.t2 = tb.b(q.sa.z, b);
+    q.t3 = tb.a(q.sb.y, a);
+    q.t4 = tb.b(q.sb.z, a);
+  } else {
+    q = swap_parts<BIG>(sm, tb, S, c, a, b);
+  }
   const int nva = q.sa.x, nvb = q.sb.x;
   const int va = nv_veh(nva), vb = nv_veh(nvb);
   const int da = q.t1 + q.t2 - q.sa.w;
@@ -664,10 +682,10 @@ __device__ __forceinline__ void eval_swap(const Smem& sm, const Tab<BIG>& tb, co
   }
   const bool tabu = (tb.tabu(vb, a) >= it) || (tb.tabu(va, b) >= it);
   const bool asp = delta < zrel;
-  const bool adm = feas && (!tabu || asp);
+  const bool adm = !near && feas && (!tabu || asp);
   const int m1 = a < b ? a : b, m2 = a < b ? b : a;
   const uint32_t id = kSwapBit | (static_cast<uint32_t>(m1) << kIdShift) | static_cast<uint32_t>(m2);
-  if (DEBUG) {
+  if (DEBUG && !near) {
     const int64_t rtot = static_cast<int64_t>(c.M) * (c.N - 2);
     const int64_t idx = rtot + static_cast<int64_t>(m1) * (2 * c.M - m1 - 1) / 2 + (m2 - m1 - 1);
     P.dbg_delta[idx] = delta;
@@ -683,6 +701,7 @@ __device__ __forceinline__ void eval_swap(const Smem& sm, const Tab<BIG>& tb, co
 struct ItemCursor {
   int r_y, r_h, s_j, s_row, s_a;  // first relocation item (y, h) and swap item (j, row, a)
   int Gq, Gr, Sq, Sr, G, H, Sn;   // grid stride in both coordinate systems, list sizes
+  int n_k;                        // first item of the neighbour pass (mission t)
 };
 
 template <bool PEN, bool DL, bool DEBUG, bool BIG, bool RP, bool HELI>
@@ -701,12 +720,22 @@ __device__ __forceinline__ uint64_t eval_items(const Smem& sm, const Tab<BIG>& t
   for (int j = q.s_j, row = q.s_row, a = q.s_a; j < q.Sn; j += q.G) {
     int b = a + row + 1;
     if (b >= c.M) b -= c.M;
-    eval_swap<PEN, DL, DEBUG, BIG, HELI>(sm, tb, S, c, a, b, it, zrel, P, key);
+    eval_swap<PEN, DL, DEBUG, BIG, HELI, RP>(sm, tb, S, c, a, b, it, zrel, P, key);
     a += q.Sr;
     row += q.Sq;
     if (a >= c.M) {
       a -= c.M;
       ++row;
+    }
+  }
+  // Swaps of neighbours, t and its successor (the batch and serving kernels only, which
+  // are bound by instruction issue: the main pass then takes the short form of every
+  // pair; the single-instance kernel, bound by the latency of its slowest warp, keeps one
+  // pass over the pairs with the neighbour case inside).
+  if (RP) {
+    for (int t = q.n_k; t < c.M; t += q.G) {
+      const int u = nv_next(S.nv(t));
+      if (u < c.M) eval_swap<PEN, DL, DEBUG, BIG, HELI, false>(sm, tb, S, c, t, u, it, zrel, P, key);
     }
   }
   return key;
@@ -1131,19 +1160,22 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
   if (looped) {
     if (C > 1) cluster_sync_all();
     // Static assignment over the item list [relocation pairs (N * ceil(M/2)) | swaps
-    // (M(M-1)/2)]: chunks of 32 consecutive items go round-robin to (CTA, warp) over the
-    // K * C CTAs of the grid, so every CTA gets an equal share and the lanes of a warp
-    // take consecutive items.
+    // (M(M-1)/2) | neighbour swaps (M, with RP records only)]: chunks of 32 consecutive items go round-robin to
+    // (CTA, warp) over the K * C CTAs of the grid, so every CTA gets an equal share and
+    // the lanes of a warp take consecutive items.
     // A relocation item i is (y, h) = divmod(i, H) for missions 2h and 2h + 1; a swap
     // item j is (row, a) = divmod(j, M) with b = (a + row + 1) mod M, which lists every
-    // pair a != b once. Coordinates advance by G without dividing.
+    // pair a != b once (with RP records the pairs that are neighbours in a route are
+    // masked there, and a neighbour item t swaps mission t with its successor when that
+    // is a mission).
+    // Coordinates advance by G without dividing.
     const int CT = K * C;
     const int G = CT * nthr;
     const int g = lane + 32 * (cid * C + rank + CT * warp);
     const int H = (M + 1) / 2;
     const int Rn = N * H;
     const int Sn = M * (M - 1) / 2;
-    int r_y = N, r_h = 0, s_j = Sn, s_row = 0, s_a = 0, Gq = 0, Gr = 0, Sq = 0, Sr = 0;
+    int r_y = N, r_h = 0, s_j = Sn, s_row = 0, s_a = 0, Gq = 0, Gr = 0, Sq = 0, Sr = 0, n_k = M;
     if (M > 0) {
       Gq = G / H;
       Gr = G - Gq * H;
@@ -1159,8 +1191,10 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
         s_row = s_j / M;
         s_a = s_j - s_row * M;
       }
+      const int k2 = g < Rn + Sn ? (Rn + Sn - g + G - 1) / G : 0;  // items before the neighbour pass
+      n_k = g + k2 * G - (Rn + Sn);
     }
-    const ItemCursor cursor{r_y, r_h, s_j, s_row, s_a, Gq, Gr, Sq, Sr, G, H, Sn};
+    const ItemCursor cursor{r_y, r_h, s_j, s_row, s_a, Gq, Gr, Sq, Sr, G, H, Sn, n_k};
     const int iters = DEBUG ? 1 : P.iterations;
     for (it = 0; it < iters; ++it) {
       const State S = sm.st(cur);
