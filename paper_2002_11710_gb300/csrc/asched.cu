@@ -104,8 +104,8 @@ __host__ __device__ inline Layout make_layout(int M, int V, int L, int nt, bool 
   }
   y.cmat = o;    o += nt * y.Mp;
   y.wm = o;      o += y.Mp;
-  y.eloc = o;    o += y.Np;
-  y.sloc = o;    o += y.Np;
+  y.eloc = o;    o += round_up(M + V + 3, 4);  // + 3: quads of missions read up to M + 2
+  y.sloc = o;    o += round_up(M + V + 3, 4);
   y.vtype = o;   o += y.Vp;
   y.tyl = o;     o += y.Vp;
   y.tym = o;     o += y.Vp;
@@ -433,6 +433,35 @@ struct Tab {
     }
     return *reinterpret_cast<const int2*>(g_smem + B + r + m0);
   }
+  // Entries of missions m0 .. m0 + 3 (m0 a multiple of 4), by 128-bit loads.
+  __device__ __forceinline__ int4 a4(int r, int m0) const {
+    if (BIG) {
+      const int4 s = *reinterpret_cast<const int4*>(g_smem + sloc + m0);
+      const int4 cm = *reinterpret_cast<const int4*>(g_smem + cmat + (r >= L ? Mp : 0) + m0);
+      const int base = r * Ls;
+      return make_int4(t16(base + s.x) + cm.x, t16(base + s.y) + cm.y, t16(base + s.z) + cm.z,
+                       t16(base + s.w) + cm.w);
+    }
+    return *reinterpret_cast<const int4*>(g_smem + A + r + m0);
+  }
+  __device__ __forceinline__ int4 b4(int r, int m0) const {
+    if (BIG) {
+      const int tyl = r >= L ? L : 0;
+      const int4 e = *reinterpret_cast<const int4*>(g_smem + eloc + m0);
+      const int col = r - tyl;
+      return make_int4(t16((tyl + e.x) * Ls + col), t16((tyl + e.y) * Ls + col), t16((tyl + e.z) * Ls + col),
+                       t16((tyl + e.w) * Ls + col));
+    }
+    return *reinterpret_cast<const int4*>(g_smem + B + r + m0);
+  }
+  __device__ __forceinline__ int4 tabu4(int v, int m0) const {
+    if (BIG) {
+      const short4 w = *reinterpret_cast<const short4*>(reinterpret_cast<const int16_t*>(g_smem + tabu_off) +
+                                                         v * Mp + m0);
+      return make_int4(w.x, w.y, w.z, w.w);
+    }
+    return *reinterpret_cast<const int4*>(g_smem + tabu_off + v * Mp + m0);
+  }
   __device__ __forceinline__ int tabu(int v, int m) const {
     if (BIG) return reinterpret_cast<const int16_t*>(g_smem + tabu_off)[v * Mp + m];
     return g_smem[tabu_off + v * Mp + m];
@@ -602,6 +631,33 @@ __device__ __forceinline__ void eval_relocate_pair(const Smem& sm, const Tab<BIG
                                         acc);
 }
 
+// Relocations of missions m0 .. m0 + 3 (m0 a multiple of 4) before node y, for the batch
+// and serving kernels: y's gap record, vehicle, flight and tabu row serve four moves, and
+// the table rows, records and stamps of the four missions come in 128-bit loads.
+template <bool PEN, bool DL, bool BIG, bool HELI>
+__device__ __forceinline__ void eval_relocate_quad(const Smem& sm, const Tab<BIG>& tb, const State& S, const Ctx& c,
+                                                   int y, int m0, int it, int zrel, const KParams& P, uint64_t& acc) {
+  const int4 r01 = *reinterpret_cast<const int4*>(S.r2() + m0);      // {nv, rem} of m0, m0 + 1
+  const int4 r23 = *reinterpret_cast<const int4*>(S.r2() + m0 + 2);  // and of m0 + 2, m0 + 3
+  const int4 rp = *reinterpret_cast<const int4*>(S.rp() + m0);
+  const int4 g = S.y4()[y];  // A row, B row, leg into y, node word of y
+  const int vy = nv_veh(g.w);
+  const int4 a4 = tb.a4(g.x, m0);
+  const int4 b4 = tb.b4(g.y, m0);
+  const int4 st = tb.tabu4(vy, m0);
+  const int fy = S.fb()[vy];
+  reloc_one<PEN, DL, false, true, HELI>(sm, S, c, y, m0, r01.x, r01.y, rp.x, g, a4.x, b4.x, fy, st.x, it, zrel, P, acc);
+  if (m0 + 1 < c.M)
+    reloc_one<PEN, DL, false, true, HELI>(sm, S, c, y, m0 + 1, r01.z, r01.w, rp.y, g, a4.y, b4.y, fy, st.y, it, zrel,
+                                          P, acc);
+  if (m0 + 2 < c.M)
+    reloc_one<PEN, DL, false, true, HELI>(sm, S, c, y, m0 + 2, r23.x, r23.y, rp.z, g, a4.z, b4.z, fy, st.z, it, zrel,
+                                          P, acc);
+  if (m0 + 3 < c.M)
+    reloc_one<PEN, DL, false, true, HELI>(sm, S, c, y, m0 + 3, r23.z, r23.w, rp.w, g, a4.w, b4.w, fy, st.w, it, zrel,
+                                          P, acc);
+}
+
 // Cost parts of swap S(a, b), each mission taking the other's place: t1 = fly from the
 // end of a's predecessor to b's pickup plus b's own leg, t2 = from b's delivery to a's
 // successor's start, t3 and t4 the same for a in b's place. When a and b are neighbours
@@ -709,7 +765,8 @@ __device__ __forceinline__ uint64_t eval_items(const Smem& sm, const Tab<BIG>& t
                                                const ItemCursor& q, int it, int zrel, const KParams& P) {
   uint64_t key = kNoKey;
   for (int y = q.r_y, h = q.r_h; y < c.N;) {
-    eval_relocate_pair<PEN, DL, DEBUG, BIG, RP, HELI>(sm, tb, S, c, y, 2 * h, it, zrel, P, key);
+    if (RP) eval_relocate_quad<PEN, DL, BIG, HELI>(sm, tb, S, c, y, 4 * h, it, zrel, P, key);
+    else eval_relocate_pair<PEN, DL, DEBUG, BIG, RP, HELI>(sm, tb, S, c, y, 2 * h, it, zrel, P, key);
     h += q.Gr;
     y += q.Gq;
     if (h >= q.H) {
@@ -921,6 +978,10 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
     sm.vtype[v] = ty;
     sm.tyl[v] = ty * L;
     sm.tym[v] = ty * Mp;
+  }
+  for (int i = N + tid; i < round_up(N + 3, 4); i += nthr) {  // padding read by quads of missions
+    sm.eloc[i] = 0;
+    sm.sloc[i] = 0;
   }
   int maxT = 0;
   if (!BIG) {  // the compact layout checks the matrix while it stages it (prologue 2)
@@ -1163,7 +1224,8 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
     // (M(M-1)/2) | neighbour swaps (M, with RP records only)]: chunks of 32 consecutive items go round-robin to
     // (CTA, warp) over the K * C CTAs of the grid, so every CTA gets an equal share and
     // the lanes of a warp take consecutive items.
-    // A relocation item i is (y, h) = divmod(i, H) for missions 2h and 2h + 1; a swap
+    // A relocation item i is (y, h) = divmod(i, H) for missions 2h and 2h + 1 (with RP
+    // records for missions 4h .. 4h + 3); a swap
     // item j is (row, a) = divmod(j, M) with b = (a + row + 1) mod M, which lists every
     // pair a != b once (with RP records the pairs that are neighbours in a route are
     // masked there, and a neighbour item t swaps mission t with its successor when that
@@ -1172,7 +1234,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
     const int CT = K * C;
     const int G = CT * nthr;
     const int g = lane + 32 * (cid * C + rank + CT * warp);
-    const int H = (M + 1) / 2;
+    const int H = RP ? (M + 3) / 4 : (M + 1) / 2;  // relocation items per node y
     const int Rn = N * H;
     const int Sn = M * (M - 1) / 2;
     int r_y = N, r_h = 0, s_j = Sn, s_row = 0, s_a = 0, Gq = 0, Gr = 0, Sq = 0, Sr = 0, n_k = M;
