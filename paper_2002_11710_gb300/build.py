@@ -32,7 +32,7 @@ def nvcc() -> str:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
-    newest = max(os.path.getmtime(x) for x in SRCS + [HDR])
+    newest = max(os.path.getmtime(x) for x in SRCS + [HDR, os.path.join(PKG, "csrc", "nvtx_range.h")])
     stale = not os.path.exists(LIB) or os.path.getmtime(LIB) < newest
     if force or stale:
         tag = f".tmp{os.getpid()}"

@@ -36,6 +36,7 @@
 #include <stdint.h>
 
 #include "asched.h"
+#include "nvtx_range.h"
 
 namespace {
 
@@ -2438,6 +2439,7 @@ KParams solve_params(const int32_t* init_route_off, const int32_t* init_route, c
 
 int asched_solve(const asched_instance* inst, const asched_params* params, const int32_t* init_route_off,
                  const int32_t* init_route, const asched_result* out, void* stream) {
+  const asched_nvtx::Range nvtx_range("asched_solve");
   if (!out || !out->route_off || !out->route || !out->info) return ASCHED_E_INVALID;
   if ((init_route_off == nullptr) != (init_route == nullptr)) return ASCHED_E_INVALID;
   return launch(inst, params, false, solve_params(init_route_off, init_route, out), nullptr, 0, false, stream);
@@ -2458,6 +2460,7 @@ int asched_workspace_bytes(const asched_instance* inst, const asched_params* par
 
 int asched_greedy_init(const asched_instance* inst, const asched_params* params, int32_t* route_off,
                        int32_t* route, int32_t* info, void* stream) {
+  const asched_nvtx::Range nvtx_range("asched_greedy_init");
   if (!params || !route_off || !route || !info) return ASCHED_E_INVALID;
   asched_params p0 = *params;
   p0.iterations = 0;
@@ -2472,6 +2475,7 @@ int asched_greedy_init(const asched_instance* inst, const asched_params* params,
 int asched_tabu_solve(const asched_instance* inst, const asched_params* params, const int32_t* init_route_off,
                       const int32_t* init_route, const asched_result* out, void* workspace, size_t workspace_bytes,
                       void* stream) {
+  const asched_nvtx::Range nvtx_range("asched_tabu_solve");
   if (!out || !out->route_off || !out->route || !out->info) return ASCHED_E_INVALID;
   if ((init_route_off == nullptr) != (init_route == nullptr)) return ASCHED_E_INVALID;
   return launch(inst, params, false, solve_params(init_route_off, init_route, out), workspace, workspace_bytes, true,
@@ -2486,11 +2490,13 @@ int asched_batch_workspace_bytes(int32_t n_instances, size_t* out) {
 
 int asched_solve_batch(const asched_batch* batch, const asched_params* params, const asched_batch_result* out,
                        void* workspace, size_t workspace_bytes, void* stream) {
+  const asched_nvtx::Range nvtx_range("asched_solve_batch");
   return launch_batch(batch, params, out, workspace, workspace_bytes, stream);
 }
 
 int asched_solve_batch_static(const asched_batch* batch, const asched_params* params,
                               const asched_batch_result* out, void* stream) {
+  const asched_nvtx::Range nvtx_range("asched_solve_batch_static");
   if (!batch) return ASCHED_E_INVALID;
   if (batch->n_instances > ASCHED_STATIC_BATCH_MAX) return ASCHED_E_TOO_LARGE;
   void* scratch = nullptr;
@@ -2511,6 +2517,7 @@ int asched_server_sizes(int32_t max_loc, int32_t max_vehicles, int32_t max_missi
 
 int asched_serve(const asched_server* server, const asched_params* params, int64_t idle_timeout_ns,
                  int32_t max_ctas, void* stream) {
+  const asched_nvtx::Range nvtx_range("asched_serve");
   return launch_serve(server, params, idle_timeout_ns, max_ctas, stream);
 }
 
@@ -2519,6 +2526,7 @@ int asched_eval_neighbourhood(const asched_instance* inst, const asched_params* 
                               int32_t it, int32_t z_best, int32_t* delta_out, uint8_t* flags_out,
                               uint32_t* id_out, unsigned long long* best_key_out, int32_t* info,
                               void* stream) {
+  const asched_nvtx::Range nvtx_range("asched_eval_neighbourhood");
   if (!route_off || !route || !delta_out || !flags_out || !best_key_out || !info) return ASCHED_E_INVALID;
   KParams kp = {};
   kp.init_off = route_off;

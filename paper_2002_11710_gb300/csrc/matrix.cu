@@ -67,6 +67,7 @@
 #include <stdint.h>
 
 #include "asched.h"
+#include "nvtx_range.h"
 
 namespace {
 
@@ -460,6 +461,7 @@ __global__ void __launch_bounds__(kThreads, 4) travel_kernel(const __grid_consta
 
 extern "C" int asched_travel_matrix(const asched_travel_spec* spec, int32_t* travel, int32_t* status,
                                     void* stream) {
+  const asched_nvtx::Range nvtx_range("asched_travel_matrix");
   if (!spec || !travel) return ASCHED_E_INVALID;
   const int B = spec->n_instances;
   if (B < 0 || spec->n_types < 1 || spec->n_types > 2) return ASCHED_E_INVALID;

@@ -22,6 +22,7 @@
 #include <stdint.h>
 
 #include "asched.h"
+#include "nvtx_range.h"
 
 namespace {
 
@@ -667,6 +668,7 @@ void* pick_sweep(bool pen, bool dl, bool tabu, bool one_warp) {
 extern "C" int asched_sweep_batch(const asched_batch* bt, int32_t algorithm, const asched_params* p,
                                   const asched_sweep_orders* orders, const asched_batch_result* out,
                                   const asched_sweep_trace* trace, void* stream) {
+  const asched_nvtx::Range nvtx_range("asched_sweep_batch");
   if (!bt || !p || !out) return ASCHED_E_INVALID;
   if (algorithm != ASCHED_SWEEP_NEIGHBOURHOOD && algorithm != ASCHED_SWEEP_TABU) return ASCHED_E_INVALID;
   if (p->tenure < 0 || p->iterations < 0 || p->lambda < 0) return ASCHED_E_INVALID;
