@@ -100,6 +100,34 @@ def test_batch_hard_cap_where_a_removal_lengthens_its_route(compact):
         np.testing.assert_array_equal(got["route_off"], r["route_off"])
 
 
+@pytest.mark.parametrize("compact", [False, True], ids=["tables", "compact"])
+def test_batch_relocation_items_of_four_missions_at_every_remainder(compact):
+    """The batch kernel evaluates relocations four missions per item: instances with every
+    mission count mod 4, with one and two vehicles (where the last item's missions run past
+    the route ends into the location arrays' padding) and with several vehicles, in both
+    layouts, HARD and PENALTY: every member equals its single solve and the oracle."""
+    insts = []
+    for s, (V, M) in enumerate([(1, 1), (1, 2), (1, 3), (1, 5), (2, 1), (2, 2), (2, 3), (2, 4),
+                                (2, 6), (2, 7), (3, 9), (5, 11), (4, 14), (6, 17)]):
+        insts.append(gen.random_instance(600 + s, n_loc=7 + V, n_vehicles=V, n_missions=M,
+                                         n_types=2, heli_only_frac=0.2 if s % 3 == 0 else 0.0,
+                                         duty_cap=100000, max_minutes=150))
+    bp = api.BatchProblem(insts)
+    for mode in (PENALTY, HARD):
+        params = api.make_params(3, 40, mode, 1000, compact=compact)
+        out = api.solve_batch(bp, params)
+        torch.cuda.synchronize()
+        for b, inst in enumerate(insts):
+            got = bp.unpack(out, b)
+            _same(got, _single(inst, params))
+            r = oracle.tabu_search(oracle.Problem(inst, mode, 1000), 3, 40)
+            assert got["info"][api.INFO_STATUS] == r["status"]
+            if r["status"] == 0:
+                assert got["info"][api.INFO_Z_BEST] == r["z_best"]
+                np.testing.assert_array_equal(got["route"], r["route"])
+                np.testing.assert_array_equal(got["route_off"], r["route_off"])
+
+
 def test_batch_result_independent_of_the_mix():
     insts = _mixed_instances()
     params = api.make_params(4, 40, PENALTY, 1000)
