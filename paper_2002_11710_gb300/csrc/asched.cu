@@ -9,16 +9,18 @@
 //
 // Design (one instance per launch):
 //   * One persistent launch runs every iteration. The grid is one thread-block
-//     cluster of C CTAs (C = 1..16), one CTA per SM. Each CTA holds a complete copy
-//     of the instance and of the search state in shared memory and applies every
-//     move itself, so the only traffic between CTAs per iteration is one 64-bit key
-//     per CTA (a relaxed DSMEM store of a key tagged with the iteration, polled by
-//     the receivers with a bounded wait).
+//     cluster of C CTAs (C = 1..16), or K such clusters for large neighbourhoods, one
+//     CTA per SM. Each CTA holds a complete copy of the instance and of the search
+//     state in shared memory and applies every move itself, so the only traffic
+//     between CTAs per iteration is one 64-bit key per CTA: a relaxed DSMEM store of a
+//     key tagged with the iteration inside a cluster, and a relaxed global store of the
+//     cluster's key between clusters, each polled by the receivers with a bounded wait.
 //   * Shared memory holds two node-by-mission gather tables built once per launch:
 //       A[t][l][m] = T_t[l][p_m] + T_t[p_m][d_m]   (fly from location l to m's pickup, then m)
 //       B[t][l][m] = T_t[d_m][l]                   (from m's delivery to location l)
 //     with the mission index innermost and rows padded to a multiple of 32 words,
-//     so that 32 lanes reading 32 consecutive missions of any row hit 32 banks.
+//     so that 32 lanes reading 32 consecutive missions of any row hit 32 banks; or,
+//     for instances whose tables do not fit, the travel matrix itself in int16.
 //   * The schedule is a doubly linked list over nodes (missions 0..M-1 and route
 //     ends M..M+V-1), with per-node records (removal delta, gap leg, slot cost,
 //     table row offsets, cap slack, deadline slacks) in a double-buffered SoA.
@@ -28,10 +30,15 @@
 //     recomputed; those the previous move changed are copied; the rest are current.
 //   * Every move (relocate (m, y) and swap (a, b)) is evaluated in O(1) from the
 //     records and the tables; the per-thread, warp (redux.sync), CTA (shared
-//     memory) and cluster (DSMEM) minimum of the key ((delta ^ 2^31) << 32) | id
-//     is independent of how moves are split over threads, so any launch shape
-//     gives the same trajectory.
+//     memory), cluster (DSMEM) and grid (L2) minimum of the key
+//     ((delta ^ 2^31) << 32) | id is independent of how moves are split over threads,
+//     so any launch shape gives the same trajectory.
 //   * The tabu list is a V x M table of iteration stamps in shared memory.
+//   * The batch and serving kernels run the same search per instance, one CTA or one
+//     cluster each, with one more record per mission (a relocation's source-route
+//     delta), relocation items of four missions and the pass over every pair of
+//     missions in its short form, the swaps of route neighbours in a pass of their own.
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
