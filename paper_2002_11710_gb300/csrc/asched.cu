@@ -23,11 +23,11 @@
 //     for instances whose tables do not fit, the travel matrix itself in int16.
 //   * The schedule is a doubly linked list over nodes (missions 0..M-1 and route
 //     ends M..M+V-1), with per-node records (removal delta, gap leg, slot cost,
-//     table row offsets, cap slack, deadline slacks) in a double-buffered SoA.
-//     Applying a move writes the other buffer in one pass (one thread per node) with
-//     no barrier between decode and write: a node's records depend only on its own
-//     route, so only the nodes of the one or two routes the move changes are
-//     recomputed; those the previous move changed are copied; the rest are current.
+//     table row offsets, cap slack, deadline slacks) in an SoA. A node's records
+//     depend only on its own links, vehicle and route flight and on static tables, so
+//     applying a move rewrites them in place, in one pass (one thread per node) after
+//     one barrier that follows the decode: only the nodes of the one or two routes
+//     the move changes are recomputed; the rest are current.
 //   * Every move (relocate (m, y) and swap (a, b)) is evaluated in O(1) from the
 //     records and the tables; the per-thread, warp (redux.sync), CTA (shared
 //     memory), cluster (DSMEM) and grid (L2) minimum of the key
@@ -62,7 +62,7 @@ constexpr int64_t kDefaultTimeoutNs = 1000000000ll;
 
 // ------------------------------------------------------------------ layout ---------
 
-// Per-node records (one buffer). A node word packs the next node and the node's
+// Per-node records. A node word packs the next node and the node's
 // vehicle word: nv = next | vw << 13, vw = vehicle | plane << 10 | heli-only << 11.
 //   R2[t] = {nv, removal delta}                       relocation, mission side
 //   Y4[t] = {A row of prev(t), B row of t, leg prev(t) -> t, nv}   relocation, gap side
@@ -83,7 +83,7 @@ constexpr int kBufWordsPerNode = 15;
 // entry is below 2^15) with a row stride of Ls halves, Ls / 2 odd, so that random rows
 // and random columns both spread over the banks; tabu stamps are int16 there too.
 struct Layout {  // offsets in int32 words from the start of dynamic shared memory
-  int A, B, tabu, cmat, wm, eloc, sloc, vtype, tyl, tym, st0, st1, best, order, cnt, gend, gdep, gfl,
+  int A, B, tabu, cmat, wm, eloc, sloc, vtype, tyl, tym, st0, best, order, cnt, gend, gdep, gfl,
       glast, misc, mbar, warpkey, slots, gkey, total;
   int Mp, Np, Vp, buf, Ls;
   bool big;
@@ -118,7 +118,6 @@ __host__ __device__ inline Layout make_layout(int M, int V, int L, int nt, bool 
   y.tyl = o;     o += y.Vp;
   y.tym = o;     o += y.Vp;
   y.st0 = o;     o += y.buf;
-  y.st1 = o;     o += y.buf;
   y.best = o;    o += y.Np;
   y.order = o;   o += y.Mp;
   y.cnt = o;     o += y.Mp;
@@ -337,7 +336,7 @@ struct Arr {  // an int32 array in shared memory
   __device__ __forceinline__ int32_t& operator[](int i) const { return g_smem[off + i]; }
 };
 
-struct State {  // one buffer of per-node records (see the layout notes)
+struct State {  // the per-node records (see the layout notes)
   int base, np, vp;
   __device__ __forceinline__ int2* r2() const { return reinterpret_cast<int2*>(g_smem + base); }
   __device__ __forceinline__ int4* y4() const { return reinterpret_cast<int4*>(g_smem + base + 2 * np); }
@@ -512,10 +511,10 @@ __device__ __forceinline__ int vw_plane(int vw) { return (vw >> 10) & 1; }
 // the vehicle part of `from` with the heli-only bit of `own`
 __device__ __forceinline__ int vw_move(int from, int own) { return (from & 0x7FF) | (own & 0x800); }
 
-// Write every record of node t into buffer S2 from its links (nx, pv), its vehicle
+// Write every record of node t into S from its links (nx, pv), its vehicle
 // word vw and the flight f2 of that vehicle.
 template <bool PEN, bool DL, bool BIG, bool RP>
-__device__ __forceinline__ void write_records(const Smem& sm, const Tab<BIG>& tb, const State& S2, const Ctx& c,
+__device__ __forceinline__ void write_records(const Smem& sm, const Tab<BIG>& tb, const State& S, const Ctx& c,
                                               int t, int nx, int pv, int vw, int f2) {
   // Every load comes before the first store: the stores go to the same shared array, so
   // the compiler could not move a load above one of them.
@@ -536,23 +535,23 @@ __device__ __forceinline__ void write_records(const Smem& sm, const Tab<BIG>& tb
     const int wt = DL ? sm.wm[t] : 0;
     const int wn = DL ? (nx < c.M ? sm.wm[nx] : c.horizon) : 0;
     const int rem = leg - slot;
-    S2.prv()[t] = pv;
-    S2.r2()[t] = make_int2(nv, rem);
+    S.prv()[t] = pv;
+    S.r2()[t] = make_int2(nv, rem);
     if (RP) {
       const int fm = f2 - c.cap;
-      S2.rp()[t] = PEN ? rem + c.lam * (pos0(fm + rem) - pos0(fm)) : (fm + rem <= 0 ? 1 : 0);
+      S.rp()[t] = PEN ? rem + c.lam * (pos0(fm + rem) - pos0(fm)) : (fm + rem <= 0 ? 1 : 0);
     }
-    S2.y4()[t] = make_int4(rowA, rowB, aT - ct, nv);
-    S2.s4()[t] = make_int4(nv, rowA, rowBn, slot);
-    if (DL) S2.d4()[t] = make_int4(dep, wt - ct, wn - cn, (dep + leg + cn <= wn) ? 1 : 0);
+    S.y4()[t] = make_int4(rowA, rowB, aT - ct, nv);
+    S.s4()[t] = make_int4(nv, rowA, rowBn, slot);
+    if (DL) S.d4()[t] = make_int4(dep, wt - ct, wn - cn, (dep + leg + cn <= wn) ? 1 : 0);
   } else {
     const int inleg = (pv == t) ? 0 : tb.b(rowB, pv);
-    S2.prv()[t] = pv;
-    S2.r2()[t] = make_int2(nv, 0);
-    S2.y4()[t] = make_int4(rowA, rowB, inleg, nv);
-    S2.s4()[t] = make_int4(nv, 0, 0, 0);
-    S2.fb()[t - c.M] = f2 - c.cap;
-    if (DL) S2.d4()[t] = make_int4(dep, c.horizon, 0, 1);
+    S.prv()[t] = pv;
+    S.r2()[t] = make_int2(nv, 0);
+    S.y4()[t] = make_int4(rowA, rowB, inleg, nv);
+    S.s4()[t] = make_int4(nv, 0, 0, 0);
+    S.fb()[t - c.M] = f2 - c.cap;
+    if (DL) S.d4()[t] = make_int4(dep, c.horizon, 0, 1);
   }
 }
 
@@ -832,31 +831,11 @@ __device__ __forceinline__ int moved_flight(const Smem& sm, const Tab<BIG>& tb, 
   return src ? f + da : f + db;
 }
 
-// Copy every record of node t from buffer S to buffer S2 (t's route is unchanged).
-template <bool DL, bool RP>
-__device__ __forceinline__ void copy_records(const State& S, const State& S2, const Ctx& c, int t) {
-  // all loads first (the stores could alias them as far as the compiler knows)
-  const int2 r2 = S.r2()[t];
-  const int4 y4 = S.y4()[t];
-  const int4 s4 = S.s4()[t];
-  const int4 d4 = DL ? S.d4()[t] : make_int4(0, 0, 0, 0);
-  const int pv = S.prv()[t];
-  const bool end = t >= c.M;
-  const int extra = end ? S.fb()[t - c.M] : (RP ? S.rp()[t] : 0);
-  S2.r2()[t] = r2;
-  S2.y4()[t] = y4;
-  S2.s4()[t] = s4;
-  if (DL) S2.d4()[t] = d4;
-  S2.prv()[t] = pv;
-  if (end) S2.fb()[t - c.M] = extra;
-  else if (RP) S2.rp()[t] = extra;
-}
-
 // ------------------------------------------------------------------ the kernel -----
 
 // The compact layout's int16 matrix, row t*L + r of layer t at T16 + (t*L + r) * Ls, zero
-// padded, built from the int32 input through a staging buffer: the second record buffer,
-// which nothing uses before the first move is applied. When the input is 16-byte aligned
+// padded, built from the int32 input through a staging buffer: the record buffer, which
+// nothing uses before the prologue writes the records. When the input is 16-byte aligned
 // its words go by bulk copies completing on an mbarrier, in chunks the size of the
 // buffer; every CTA copies every chunk into its own shared memory (the cluster reads the
 // matrix from L2 C times; 230 KB per CTA once per solve). A block barrier after each
@@ -889,7 +868,7 @@ __device__ __forceinline__ bool stage_matrix16(const KParams& P, const Layout& l
   bool gave_up = false;  // this CTA's wait ran out
   uint32_t phase = 0;
   if (bulk > 0) {
-    int32_t* stage = g_smem + lay.st1;
+    int32_t* stage = g_smem + lay.st0;
     const int cap = lay.buf & ~3;
     const uint32_t bar = smem_u32(g_smem + lay.mbar);
     if (tid == 0) {
@@ -1222,9 +1201,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
   }
 
   // ---- main loop
-  int zbest = Z, best_it = -1, it = 0, cur = 0;
-  int pva = -1, pvb = -1;  // vehicles of the last applied move
-  bool first_move = true;
+  int zbest = Z, best_it = -1, it = 0;
   const bool looped = status == ASCHED_OK;  // uniform over the cluster
   if (looped) {
     if (C > 1) cluster_sync_all();
@@ -1267,7 +1244,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
     const ItemCursor cursor{r_y, r_h, s_j, s_row, s_a, Gq, Gr, Sq, Sr, G, H, Sn, n_k};
     const int iters = DEBUG ? 1 : P.iterations;
     for (it = 0; it < iters; ++it) {
-      const State S = sm.st(cur);
+      const State S = S0;
       const int it_eval = DEBUG ? P.dbg_it : it;
       const int zb_eval = DEBUG ? P.dbg_zbest : zbest;
       // z_best - Z, clamped to int32 (a caller's z_best is arbitrary in DEBUG mode; every
@@ -1393,13 +1370,11 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
       if (DEBUG) {
         if (lead && tid == 0 && !timed_out) *P.dbg_key = gk;
       } else if (!timed_out && !bad_key && gk != kNoKey) {
-        // ---- apply the chosen move. Records go into the other buffer, and a node's
-        // records depend only on its own route, so only the nodes of the one or two routes
-        // the move changes (vehicles va, vb) are recomputed there; the nodes the previous
-        // applied move changed (vehicles pva, pvb), stale in that buffer, are copied over;
-        // every other node's records there are current already. Before the first applied
-        // move the other buffer holds nothing, so every node is copied.
-        const State S2 = sm.st(cur ^ 1);
+        // ---- apply the chosen move, in place. A node's records depend only on its own
+        // links, vehicle and route flight, and static tables: every thread first reads
+        // the move's records (the decode and the two routes' new flights), then, after
+        // one barrier, rewrites the nodes of the one or two changed routes (vehicles va,
+        // vb), each thread its own nodes.
         const int Znew = Z + key_delta(gk);
         const bool improved = Znew < zbest;
         const uint32_t id = static_cast<uint32_t>(gk);
@@ -1414,6 +1389,9 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
         const int x1 = nv_next(nv1), x2 = nv_next(nv2);
         const bool adjA = is_swap && x1 == n2;  // a immediately before b
         const bool adjB = is_swap && x2 == n1;  // b immediately before a
+        const int f_src = moved_flight<BIG>(sm, tb, S, c, id, true);
+        const int f_dst = moved_flight<BIG>(sm, tb, S, c, id, false);
+        __syncthreads();  // no record is rewritten before every thread has read the move's
         for (int t = tid; t < N; t += nthr) {
           const int nv = S.nv(t);
           const int vt = nv_veh(nv);
@@ -1474,11 +1452,8 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
             }
             // The new flight of t's route is needed by route ends (FB) and, with RP
             // records, by every mission.
-            int f2 = 0;
-            if (RP || t >= M) f2 = moved_flight<BIG>(sm, tb, S, c, id, vw_veh(vw) == va);
-            write_records<PEN, DL, BIG, RP>(sm, tb, S2, c, t, nx, pv, vw, f2);
-          } else if (first_move || vt == pva || vt == pvb) {
-            copy_records<DL, RP>(S, S2, c, t);
+            const int f2 = vw_veh(vw) == va ? f_src : f_dst;
+            write_records<PEN, DL, BIG, RP>(sm, tb, S, c, t, nx, pv, vw, f2);
           }
           if (improved) sm.best[t] = nx;
         }
@@ -1486,9 +1461,6 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
           tb.set_tabu(va, n1, it + P.tenure);
           if (is_swap) tb.set_tabu(vb, n2, it + P.tenure);
         }
-        pva = va;
-        pvb = vb;
-        first_move = false;
         Z = Znew;
         if (improved) {
           zbest = Znew;
@@ -1503,7 +1475,6 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
         status = bad_key ? ASCHED_E_INVALID : ASCHED_E_TIMEOUT;
         break;
       }
-      if (!DEBUG && gk != kNoKey) cur ^= 1;
     }
   }
 

@@ -343,7 +343,10 @@ def test_large_instance_sampled_against_oracle():
     iters = 120
     dp = api.DeviceProblem(inst)
     params = api.params_from(p, iterations=iters)
-    assert api.plan(dp, params).smem_bytes > 200 * 1024
+    # the gather tables alone (2 x L x M rounded up to 32, int32) exceed a CTA's shared
+    # memory, so the plan that launches is the int16 matrix layout
+    assert 2 * inst.n_loc * ((inst.n_missions + 31) // 32 * 32) * 4 > 232448
+    assert api.plan(dp, params).smem_bytes <= 232448
     out = api.solve(dp, params, trajectory=True)
     torch.cuda.synchronize()
     info = out.info.cpu().numpy()
