@@ -352,7 +352,7 @@ struct Smem {
   Arr A, B, tabu, cmat, wm, eloc, sloc, vtype, tyl, tym, best, order, cnt, gend, gdep, gfl, glast, misc;
   int st0, buf, np, vp;
   int warpkey_off, slots_off, gkey_off;
-  __device__ __forceinline__ State st(int k) const { return State{st0 + k * buf, np, vp}; }
+  __device__ __forceinline__ State records() const { return State{st0, np, vp}; }  // the per-node records
   __device__ __forceinline__ uint64_t* warpkey() const {
     return reinterpret_cast<uint64_t*>(g_smem + warpkey_off);
   }
@@ -1000,7 +1000,7 @@ __device__ __forceinline__ void solve_one(const KParams& P, const Layout& lay, c
   }
 
   // ---- prologue 2: gather tables, in-mission legs, tabu stamps, route ends
-  const State S0 = sm.st(0);
+  const State S0 = sm.records();
   if (status == ASCHED_OK) {
     if (!BIG) {
       for (int i = tid; i < nt * L * Mp; i += nthr) {
